@@ -1,0 +1,407 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+- exact lattice arithmetic against Python's exact rationals (fractions.Fraction);
+- the triangle primitives against closed forms and against an exhaustive active-set
+  solution of the distance QP (every pair of sub-simplices), and scipy's SLSQP;
+- the BVH traversal of Algorithm 1 against brute force over all triangle pairs;
+- CD/PQ against closed-form box-box distances and a convex-hull QP;
+- the encoding against its invariants (conservative, nested, in range) and the
+  independent blob decoder;
+- the near-contact filter against a brute-force recomputation.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+DIRS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1),
+        (0, 1, -1), (1, 1, 1), (1, 1, -1), (1, -1, 1), (-1, 1, 1)]
+
+
+# ------------------------------------------------------------------ exact lattice
+def _frac_floor(x: Fraction) -> int:
+    return math.floor(x)
+
+
+def test_floor_sum3_matches_exact_rationals():
+    rng = np.random.default_rng(7)
+    cases = []
+    for _ in range(3000):
+        e = rng.integers(-60, 60, size=3)
+        v = rng.uniform(-1, 1, size=3) * np.exp2(e)
+        cases.append(tuple(float(x) for x in v))
+    # adversarial: integers plus tiny residues of either sign, cancellation, huge spread
+    for k in range(1, 40):
+        t = 2.0 ** -k
+        cases += [(5.0, t, -t), (5.0, -t, 0.0), (5.0, t, 0.0), (-3.0, 1.0 - t, -t), (2.0 ** 29, -0.5, -t),
+                  (1e16, -1e16, t), (1e16, -1e16, -t), (7.5, 0.5, -2.0 ** -1074)]
+    for a, b, c in cases:
+        exact = Fraction(a) + Fraction(b) + Fraction(c)
+        assert oracle.floor_sum3(a, b, c) == _frac_floor(exact), (a, b, c)
+        assert oracle.ceil_sum3(a, b, c) == math.ceil(exact), (a, b, c)
+
+
+def test_lattice_dv_matches_exact_rationals():
+    rng = np.random.default_rng(8)
+    for _ in range(2000):
+        v = (rng.uniform(-3, 3, size=3) * np.exp2(rng.integers(-20, 3, size=3))).astype(np.float32)
+        j = int(rng.integers(0, 13))
+        e = int(rng.integers(-40, -10))
+        d = DIRS[j]
+        x = sum(Fraction(int(d[c])) * Fraction(float(v[c])) for c in range(3)) / Fraction(2) ** e
+        lo, hi = oracle.lattice_dv(v, j, e)
+        assert lo == math.floor(x) and hi == math.ceil(x)
+
+
+def _tiny_mesh(seed, n=40):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, size=(n, 1, 3))
+    v = (c + rng.uniform(-0.2, 0.2, size=(n, 3, 3))).reshape(-1, 3).astype(np.float32)
+    return v, np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+
+
+@pytest.mark.parametrize("k,m,bits", [(6, 2, 8), (18, 4, 16), (24, 8, 8), (26, 16, 16), (18, 4, 0)])
+def test_exact_node_lattice_and_exponent(k, m, bits):
+    v, t = _tiny_mesh(3 + k + m)
+    h = oracle.BVH(v, t, k, m, bits, 4096)
+    K = k // 2
+    # exponent: smallest e with |d.v| / 2^e < 2^30 for every used vertex and direction
+    vals = [sum(Fraction(d[c]) * Fraction(float(p[c])) for c in range(3)) for p in v for d in DIRS[:K]]
+    M = max(abs(x) for x in vals)
+    assert M / Fraction(2) ** h.e < 2 ** 30
+    assert not (M / Fraction(2) ** (h.e - 1) < 2 ** 30)
+    tr = h.tree()
+    lat = h.lattice()["exact"]
+    # the triangle set of every node, from the tree
+    sets = [None] * h.n_nodes
+    for x in range(h.n_nodes - 1, -1, -1):
+        if tr["nchild"][x] == 0:
+            sets[x] = [int(tr["tri"][x])]
+        else:
+            sets[x] = sum((sets[tr["first"][x] + c] for c in range(tr["nchild"][x])), [])
+    assert sorted(sets[0]) == list(range(len(t)))
+    scale = Fraction(2) ** h.e
+    for x in range(h.n_nodes):
+        pts = [v[i] for tri in sets[x] for i in t[tri]]
+        for j in range(K):
+            xs = [sum(Fraction(DIRS[j][c]) * Fraction(float(p[c])) for c in range(3)) / scale for p in pts]
+            assert lat[x, j, 0] == math.floor(min(xs)) and lat[x, j, 1] == math.ceil(max(xs))
+
+
+def _centroid_keys(v, t):
+    p = v[t].astype(np.float64)
+    return (p[:, 0] + p[:, 1]) + p[:, 2]
+
+
+@pytest.mark.parametrize("m", [2, 4, 8, 16])
+def test_tree_split_properties(m):
+    """Every inner node has min(n, m) children, child sizes come from repeated floor/ceil
+    halving, and each binary split separates its halves along the axis of largest
+    centroid extent (checked by regrouping the children in split order)."""
+    v, t = synth.icosphere(2, 1.0, 0.15, seed=11)
+    h = oracle.BVH(v, t, 18, m, 16, 4096)
+    tr = h.tree()
+    key = _centroid_keys(v, t)
+    sets = [None] * h.n_nodes
+    for x in range(h.n_nodes - 1, -1, -1):
+        if tr["nchild"][x] == 0:
+            sets[x] = [int(tr["tri"][x])]
+        else:
+            sets[x] = sum((sets[tr["first"][x] + c] for c in range(tr["nchild"][x])), [])
+
+    def check_split(groups):
+        # groups: list of triangle lists in split order that came from one group of the
+        # previous round; reconstruct the binary tree of splits bottom-up
+        if len(groups) == 1:
+            return groups[0]
+        n = sum(len(g) for g in groups)
+        left_n = n // 2
+        acc, cut = 0, 0
+        while acc < left_n:
+            acc += len(groups[cut])
+            cut += 1
+        assert acc == left_n
+        L, R = check_split(groups[:cut]), check_split(groups[cut:])
+        both = L + R
+        ext = key[both].max(0) - key[both].min(0)
+        ax = int(np.argmax(ext))  # first maximum: ties resolved x < y < z
+        kl = sorted((key[i, ax], i) for i in L)
+        kr = sorted((key[i, ax], i) for i in R)
+        assert kl[-1] < kr[0]
+        return both
+
+    for x in range(h.n_nodes):
+        nc = tr["nchild"][x]
+        if nc == 0:
+            assert len(sets[x]) == 1
+            continue
+        n = len(sets[x])
+        assert nc == min(n, m)
+        check_split([sets[tr["first"][x] + c] for c in range(nc)])
+
+
+@pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
+                                         (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536)])
+def test_encoding_invariants(k, m, bits, tb):
+    v, t = synth.icosphere(3, 1.0, 0.15, seed=5)
+    h = oracle.BVH(v, t, k, m, bits, tb)
+    tr = h.tree()
+    L = h.lattice()
+    ex, dec, decf = L["exact"], L["decoded"], L["decf"]
+    pl = h.placement()
+    # conservative and nested
+    assert (dec[..., 0] <= ex[..., 0]).all() and (dec[..., 1] >= ex[..., 1]).all()
+    par = tr["parent"][1:]
+    assert (dec[1:, :, 0] >= dec[par, :, 0]).all() and (dec[1:, :, 1] <= dec[par, :, 1]).all()
+    # correctors fit b bits
+    if bits:
+        assert pl["delta"].max() <= (1 << bits) - 1
+    # the FP32 bounds contain the exact real bounds d.v of every vertex of the node
+    e = h.e
+    for x in range(0, h.n_nodes, 7):
+        assert (decf[x, :, 0].astype(np.float64) <= np.ldexp(ex[x, :, 0].astype(np.float64), e)).all()
+        assert (decf[x, :, 1].astype(np.float64) >= np.ldexp(ex[x, :, 1].astype(np.float64), e)).all()
+    # treelet roots (local 0) are exact; nodes of one treelet stay within the byte budget
+    roots = pl["local"] == 0
+    assert (dec[roots] == ex[roots]).all()
+    counts = np.bincount(pl["treelet"])
+    assert (16 + h.root_bytes + (counts - 1) * h.rec_bytes <= tb).all()
+    # the independent decoder reproduces the encoder, node by node
+    lat, f, meta = oracle.decode_blob(h.blob())
+    order = np.lexsort((pl["local"], pl["treelet"]))
+    if bits:
+        assert (lat == dec[order]).all()
+    assert (f.view(np.uint32) == decf[order].view(np.uint32)).all()
+    assert ((meta[:, 0] >> 16) & 31 == tr["nchild"][order]).all()
+
+
+def test_bad_arguments_and_meshes():
+    v, t = synth.icosphere(1, seed=1)
+    for args in [(5, 4, 8, 4096), (18, 3, 8, 4096), (18, 4, 12, 4096), (18, 4, 8, 5000), (18, 4, 8, 2048)]:
+        with pytest.raises(oracle.OracleError):
+            oracle.BVH(v, t, *args)
+    bad = t.copy()
+    bad[0, 0] = len(v)
+    with pytest.raises(oracle.OracleError):
+        oracle.BVH(v, bad, 18, 4, 8, 4096)
+    deg = t.copy()
+    deg[0] = (0, 0, 1)
+    with pytest.raises(oracle.OracleError):
+        oracle.BVH(v, deg, 18, 4, 8, 4096)
+
+
+# ------------------------------------------------------------------ triangle primitives
+def _qp_exact(V, U):
+    """Triangle-triangle distance by exhaustive active sets: for every pair of non-empty
+    vertex subsets, minimise over their affine hulls; keep solutions with non-negative
+    barycentric weights.  The optimum of the convex QP lies in the relative interior of
+    some face pair, where it equals that affine minimum."""
+    best = math.inf
+    subsets = [s for r in (1, 2, 3) for s in itertools.combinations(range(3), r)]
+    for S in subsets:
+        for T in subsets:
+            E = np.array([V[i] - V[S[0]] for i in S[1:]]).reshape(-1, 3).T
+            F = np.array([U[j] - U[T[0]] for j in T[1:]]).reshape(-1, 3).T
+            M = np.concatenate([E, -F], axis=1)
+            r0 = V[S[0]] - U[T[0]]
+            if M.shape[1]:
+                x, *_ = np.linalg.lstsq(M, -r0, rcond=None)
+            else:
+                x = np.zeros(0)
+            a, b = x[:len(S) - 1], x[len(S) - 1:]
+            lam = np.concatenate([[1 - a.sum()], a])
+            mu = np.concatenate([[1 - b.sum()], b])
+            if lam.min() < -1e-12 or mu.min() < -1e-12:
+                continue
+            best = min(best, float(np.linalg.norm(r0 + M @ x)))
+    return best
+
+
+def test_tri_primitives_closed_forms():
+    T = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], float)
+    for h in (0.5, 1e-3, 2.0):
+        U = T + [0, 0, h]
+        assert oracle.tri_dist(T, U) == pytest.approx(h, rel=1e-14)
+        assert not oracle.tri_intersect(T, U)[0]
+    # coplanar overlap and coplanar separation (gap along x of 0.25)
+    assert oracle.tri_intersect(T, T + [0.2, 0.2, 0])[0]
+    U = np.array([[1.25, 0, 0], [2, 0, 0], [1.25, 1, 0]], float)
+    assert not oracle.tri_intersect(T, U)[0]
+    assert oracle.tri_dist(T, U) == pytest.approx(0.25, rel=1e-14)
+    # a vertical triangle piercing T
+    U = np.array([[0.2, 0.2, -1], [0.3, 0.2, 1], [0.2, 0.3, 1]], float)
+    assert oracle.tri_intersect(T, U)[0] and oracle.tri_dist(T, U) == 0.0
+    # touching at a single point (closed): vertex of U on T's interior
+    U = np.array([[0.2, 0.2, 0], [0.2, 0.2, 1], [0.3, 0.4, 1]], float)
+    assert oracle.tri_intersect(T, U)[0]
+    # skew edges: edge x-axis segment vs a segment parallel to y at height z=h, x=0.5
+    h = 0.3
+    U = np.array([[0.5, -1, h], [0.5, -2, h + 5], [0.5, -0.0001, h + 5]], float)
+    # closest features: T's edge (0,0,0)-(1,0,0) and U's edge from (0.5,-1,h) .. -> distance
+    d = oracle.tri_dist(T, U)
+    assert d == pytest.approx(_qp_exact(T, U), abs=1e-12)
+    # segment-segment closed form: perpendicular skew lines at distance h
+    assert oracle.seg_seg([0, 0, 0], [1, 0, 0], [0.5, -1, h], [0.5, 1, h]) == pytest.approx(h, rel=1e-14)
+    # parallel segments, offset: endpoint-to-segment
+    assert oracle.seg_seg([0, 0, 0], [1, 0, 0], [2, 1, 0], [3, 1, 0]) == pytest.approx(math.sqrt(2), rel=1e-14)
+    # point above the interior / beyond a vertex
+    assert oracle.pt_tri([0.2, 0.2, 0.7], T) == pytest.approx(0.7, rel=1e-14)
+    assert oracle.pt_tri([-3, -4, 0], T) == pytest.approx(5.0, rel=1e-14)
+
+
+def test_tri_primitives_against_exhaustive_qp():
+    rng = np.random.default_rng(123)
+    n_hit = n_miss = 0
+    for _ in range(600):
+        V = rng.uniform(-1, 1, size=(3, 3))
+        U = rng.uniform(-1, 1, size=(3, 3)) * rng.uniform(0.2, 1.5) + rng.uniform(-0.8, 0.8, size=3)
+        hit, margin = oracle.tri_intersect(V, U)
+        d = oracle.tri_dist(V, U)
+        q = _qp_exact(V, U)
+        if hit:
+            if margin < 1e-6:
+                continue
+            n_hit += 1
+            assert d == 0.0 and q < 1e-9
+        else:
+            n_miss += 1
+            assert q > 0 and d == pytest.approx(q, rel=1e-9, abs=1e-12)
+    assert n_hit > 50 and n_miss > 50
+
+
+def test_tri_dist_against_slsqp():
+    opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(9)
+    for _ in range(40):
+        V = rng.uniform(-1, 1, size=(3, 3))
+        U = rng.uniform(-1, 1, size=(3, 3)) + rng.uniform(1.0, 2.0, size=3)
+        f = lambda z: float(np.sum((z[:3] @ V - z[3:] @ U) ** 2))  # noqa: E731
+        cons = [{"type": "eq", "fun": lambda z: z[:3].sum() - 1}, {"type": "eq", "fun": lambda z: z[3:].sum() - 1}]
+        r = opt.minimize(f, np.full(6, 1 / 3), method="SLSQP", bounds=[(0, 1)] * 6, constraints=cons,
+                         options={"ftol": 1e-16, "maxiter": 500})
+        assert oracle.tri_dist(V, U) == pytest.approx(math.sqrt(r.fun), rel=1e-5, abs=1e-8)
+
+
+# ------------------------------------------------------------------ traversal pins
+@pytest.fixture(scope="module")
+def c1_small():
+    c = synth.C1(24)
+    A = oracle.BVH(*c["A"], 18, 4, 16, 4096)
+    B = oracle.BVH(*c["B"], 18, 4, 16, 4096)
+    return c, A, B
+
+
+def test_algorithm1_cd_equals_brute_force(c1_small):
+    c, A, B = c1_small
+    hit, off, ij, st = oracle.collide(A, B, c["poses"])
+    hb, ob, ijb = oracle.brute_collide(A, B, c["poses"])
+    assert hit.sum() > 3 and (hit == 0).sum() > 3
+    assert (hit == hb).all() and (off == ob).all() and (ij == ijb).all()
+    # compressed (decoded FP32) bounding volumes prune to the same answer
+    hd, od, ijd, std = oracle.collide(A, B, c["poses"], use_decoded=True)
+    assert (hd == hit).all() and (od == off).all() and (ijd == ij).all()
+    assert st["bv_tests"] > 0 and std["bv_tests"] >= st["bv_tests"] * 0.9
+
+
+def test_algorithm1_pq_equals_brute_force(c1_small):
+    c, A, B = c1_small
+    d, _ = oracle.distance(A, B, c["poses"])
+    db = oracle.brute_distance(A, B, c["poses"])
+    dd, _ = oracle.distance(A, B, c["poses"], use_decoded=True)
+    assert (d == db).all() and (dd == db).all()
+    hit, *_ = oracle.collide(A, B, c["poses"])
+    assert ((d == 0) == (hit == 1)).all()
+
+
+def test_box_box_closed_form():
+    va, ta = synth.box_mesh((1.0, 0.6, 0.4))
+    vb, tb = synth.box_mesh((0.5, 0.5, 0.5))
+    A = oracle.BVH(va, ta, 18, 4, 16, 4096)
+    B = oracle.BVH(vb, tb, 18, 4, 16, 4096)
+    rng = np.random.default_rng(4)
+    # half sizes of the two boxes as the FP32 meshes store them
+    half = np.abs(va.astype(np.float64)).max(0) + np.abs(vb.astype(np.float64)).max(0)
+    P, expect = [], []
+    while len(P) < 60:
+        tr = rng.uniform(-1.5, 1.5, size=3)
+        gap = np.abs(tr) - half
+        if (gap > 1e-3).any():
+            expect.append(float(np.linalg.norm(np.maximum(gap, 0))))
+        elif (np.abs(gap) > 1e-3).all() and (gap < 0).all() and ((np.abs(tr) + 0.25 > np.array([0.5, 0.3, 0.2])).any()):
+            expect.append(0.0)
+        else:
+            continue
+        P.append(np.concatenate([np.eye(3).ravel(), tr]))
+    P = np.array(P, np.float32)
+    d, _ = oracle.distance(A, B, P)
+    hit, *_ = oracle.collide(A, B, P)
+    tr = P[:, 9:].astype(np.float64)
+    exp = np.linalg.norm(np.maximum(np.abs(tr) - half, 0), axis=1)
+    assert np.allclose(d, exp, rtol=1e-12, atol=1e-12)
+    assert ((hit == 1) == (exp == 0)).all()
+
+
+def test_convex_icospheres_against_hull_qp():
+    opt = pytest.importorskip("scipy.optimize")
+    va, ta = synth.icosphere(1, 1.0, 0.0, seed=1)
+    vb, tb = synth.icosphere(1, 0.7, 0.0, seed=2)
+    A = oracle.BVH(va, ta, 24, 8, 8, 16384)
+    B = oracle.BVH(vb, tb, 24, 8, 8, 16384)
+    P = synth.poses_box(6, seed=77, lo=1.0, hi=1.6)
+    d, _ = oracle.distance(A, B, P)
+    for p, dp in zip(P, d):
+        R, t = p[:9].reshape(3, 3).astype(np.float64), p[9:].astype(np.float64)
+        wb = vb.astype(np.float64) @ R.T + t
+        na, nb = len(va), len(wb)
+        Va = va.astype(np.float64)
+
+        def f(z):
+            r = z[:na] @ Va - z[na:] @ wb
+            return float(r @ r)
+
+        def g(z):
+            r = z[:na] @ Va - z[na:] @ wb
+            return np.concatenate([2 * Va @ r, -2 * wb @ r])
+        cons = [{"type": "eq", "fun": lambda z: z[:na].sum() - 1, "jac": lambda z: np.r_[np.ones(na), np.zeros(nb)]},
+                {"type": "eq", "fun": lambda z: z[na:].sum() - 1, "jac": lambda z: np.r_[np.zeros(na), np.ones(nb)]}]
+        z0 = np.r_[np.full(na, 1 / na), np.full(nb, 1 / nb)]
+        r = opt.minimize(f, z0, jac=g, method="SLSQP", bounds=[(0, 1)] * (na + nb), constraints=cons,
+                         options={"ftol": 1e-15, "maxiter": 1000})
+        assert dp > 0
+        assert dp == pytest.approx(math.sqrt(max(r.fun, 0)), rel=1e-4, abs=1e-6)
+
+
+def test_near_contact_filter_against_brute_force(c1_small):
+    c, A, B = c1_small
+    va, ta = c["A"]
+    vb, tb = c["B"]
+    D = synth.scene_diameter(va, vb)
+    eps = 1e-3 * D  # a wide band so that several poses are flagged
+    near, margin = oracle.near_contact(A, B, c["poses"][:10], eps)
+    for p in range(10):
+        pose = c["poses"][p]
+        R, t = pose[:9].reshape(3, 3).astype(np.float64), pose[9:].astype(np.float64)
+        TA = va.astype(np.float64)[ta]
+        TB = vb.astype(np.float64)[tb] @ R.T + t
+        lo_a, hi_a = TA.min(1), TA.max(1)
+        lo_b, hi_b = TB.min(1), TB.max(1)
+        flagged = False
+        mmin = math.inf
+        for i in range(len(TA)):
+            ok = ((lo_a[i] - eps <= hi_b) & (lo_b <= hi_a[i] + eps)).all(1)
+            for j in np.nonzero(ok)[0]:
+                hit, m = oracle.tri_intersect(TA[i], TB[j])
+                q = m if hit else oracle.tri_dist(TA[i], TB[j])
+                mmin = min(mmin, q)
+                if (hit and m < eps) or (not hit and q <= eps):
+                    flagged = True
+        assert flagged == bool(near[p])
+        if math.isfinite(mmin) and mmin <= eps:
+            assert margin[p] == pytest.approx(mmin, rel=1e-12)
