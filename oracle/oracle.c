@@ -535,7 +535,7 @@ static int encode(or_bvh *h) {
   h->lbits = 1;
   while ((1 << h->lbits) < maxn) ++h->lbits;
   if (maxn > 65535) return fail(OR_ERR_ARG, "too many nodes in one treelet");
-  if (h->lbits < 32 && (uint64_t)h->ntlet > ((uint64_t)1 << (32 - h->lbits)))
+  if (h->lbits < 32 && (uint64_t)h->ntlet >= ((uint64_t)1 << (32 - h->lbits)))
     return fail(OR_ERR_ARG, "too many treelets for 32-bit node references");
 
   /* Predictor-corrector (abstract, Sec. III-B): a treelet root is absolute; any other node
@@ -615,9 +615,12 @@ static int encode(or_bvh *h) {
   put64(B + 48, (uint64_t)off_tris);
   put64(B + 56, (uint64_t)total);
   for (int64_t t = 0; t <= h->ntlet; ++t) put64(B + off_tab + 8 * t, (uint64_t)toff[t]);
+  int64_t first_node = 0;
   for (int64_t t = 0; t < h->ntlet; ++t) {
     uint8_t *T = B + toff[t];
     put32(T, (uint32_t)h->tlet_count[t]);
+    put32(T + 4, (uint32_t)first_node); /* blob-order index of the treelet's root */
+    first_node += h->tlet_count[t];
     for (int32_t l = 0; l < h->tlet_count[t]; ++l) {
       int32_t x = h->tlet_nodes[t][l];
       uint8_t *R = T + 16 + (l == 0 ? 0 : h->root_bytes + (int64_t)(l - 1) * h->rec_bytes);
@@ -761,6 +764,10 @@ int64_t or_decode_blob(const uint8_t *blob, int64_t bytes, int32_t *lat, float *
     int64_t off = (int64_t)get64(blob + 64 + 8 * t);
     const uint8_t *T = blob + off;
     int32_t cnt = (int32_t)get32(T);
+    if ((int64_t)get32(T + 4) != n) {
+      free(P);
+      return fail(OR_ERR_ARG, "treelet header: wrong first-node index");
+    }
     for (int32_t l = 0; l < cnt; ++l, ++n) {
       const uint8_t *R = T + 16 + (l == 0 ? 0 : rootb + (int64_t)(l - 1) * rec);
       uint32_t w0 = get32(R), w1 = get32(R + 4);
@@ -1187,6 +1194,39 @@ static void bvh_traversal(tctx *c, int mode, int32_t a, int32_t b) {
   }
 }
 
+/* Branch and bound for PQ: Algorithm 1's recursion with the overlap test replaced by
+ * "lower bound below the best distance so far"; the candidate pairs of one expansion are
+ * visited in increasing lower-bound order and re-checked before each descent, which changes
+ * how much is visited but not the minimum found. */
+typedef struct {
+  double lb;
+  int32_t a, b;
+} cand;
+static int cmp_cand(const void *x, const void *y) {
+  double p = ((const cand *)x)->lb, q = ((const cand *)y)->lb;
+  return (p > q) - (p < q);
+}
+static void bvh_pq(tctx *c, int32_t a, int32_t b) {
+  const or_bvh *A = c->A, *B = c->B;
+  int la = A->nchild[a] == 0, lb_ = B->nchild[b] == 0;
+  if (la && lb_) {
+    check_primitives(c, MODE_PQ, a, b);
+    return;
+  }
+  int na = la ? 1 : A->nchild[a], nb = lb_ ? 1 : B->nchild[b];
+  cand cs[256];
+  int n = 0;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j) {
+      int32_t ai = la ? a : A->first[a] + i, bj = lb_ ? b : B->first[b] + j;
+      double l = bv_lower(c, ai, bj);
+      if (l < c->best) cs[n++] = (cand){l, ai, bj};
+    }
+  qsort(cs, (size_t)n, sizeof(cand), cmp_cand);
+  for (int q = 0; q < n && c->best > 0; ++q)
+    if (cs[q].lb < c->best) bvh_pq(c, cs[q].a, cs[q].b);
+}
+
 typedef struct {
   int64_t n;
   pvec *v;
@@ -1252,7 +1292,7 @@ void or_distance(const or_bvh *A, const or_bvh *B, const float *poses, int64_t n
   for (int64_t p = 0; p < n; ++p) {
     tctx c;
     ctx_init(&c, A, B, poses + 12 * p, use_decoded, 0.0);
-    if (bv_lower(&c, 0, 0) < c.best) bvh_traversal(&c, MODE_PQ, 0, 0);
+    if (bv_lower(&c, 0, 0) < c.best) bvh_pq(&c, 0, 0);
     dist[p] = c.best;
     bv += c.bv_tests;
     lf += c.leaf_tests;
