@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the compressed k-DOP BVH engine: batched collision detection (CD) and
+proximity query (PQ) of many rigid poses on one GB300.
+
+Workload (terrain against sphere, 10,000 poses): A = 512 x 512 fractal heightfield (524,288
+triangles) and B = displaced level-5 icosphere (20,480 triangles); 24-DOP, branching 8,
+8-bit predictor-corrector deltas, 16 KB treelets.  One step = CD with every intersecting
+triangle pair (sorted CSR lists) for all poses, then PQ (minimum distance) for all poses.
+Metric: pose queries/s, a CD query and a PQ query of one pose counting as two.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
+bounded sample of the same poses.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pose queries/s (CD and PQ) + BV-pair tests/s on 1 GB300, % of HBM roofline; p50/p99"
+K_DOP, BRANCH, BITS, TREELET = 24, 8, 8, 16384
+# algorithmic bytes per unit of work for this configuration (24-DOP, 8-bit deltas):
+# one BV-pair test reads an A-member descriptor (12 slabs x 2 x 1 B + 4 B topology) and a
+# B-member axis box (3 slabs x 2 x 1 B); one leaf test reads two 36-byte triangles; one pose
+# reads 48 bytes of pose and writes 1 B flag + 4 B distance + 8 B offset.
+BYTES_BV = 24 + 4 + 6
+BYTES_LEAF = 72
+BYTES_POSE = 48 + 1 + 4 + 8
+BYTES_PAIR = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--poses", type=int, default=10000)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="poses in the oracle sample (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload(n_poses: int, rank: int):
+    c = synth.C2(n_poses)
+    if rank:  # weak scaling: every rank gets its own poses of the same distribution
+        c["poses"] = synth.poses_terrain(n_poses, seed=2002 + 7919 * rank, height_fn=c["height"])
+    return c
+
+
+# ------------------------------------------------------------------ CPU (oracle) timing
+def oracle_rate(c, sample: int, target_s: float = 15.0):
+    """Pose queries/s of the FP64 oracle (CD with pairs + PQ) on a bounded sample; the
+    sample grows until it takes about target_s seconds or reaches `sample` poses."""
+    import oracle
+    A = oracle.BVH(*c["A"], K_DOP, BRANCH, BITS, TREELET)
+    B = oracle.BVH(*c["B"], K_DOP, BRANCH, BITS, TREELET)
+    P = c["poses"]
+    n, done, t_tot = 16, 0, 0.0
+    while True:
+        take = P[done:done + n]
+        t0 = time.perf_counter()
+        oracle.collide(A, B, take)
+        oracle.distance(A, B, take)
+        t_tot += time.perf_counter() - t0
+        done += len(take)
+        if t_tot >= target_s or done >= len(P) or (sample and done >= sample):
+            break
+        n = min(len(P) - done, max(16, int(n * 2)))
+        if sample:
+            n = min(n, sample - done)
+    return 2 * done / t_tot, done, t_tot, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    c = workload(args.poses, 0)
+    import oracle
+    A = oracle.BVH(*c["A"], K_DOP, BRANCH, BITS, TREELET)
+    B = oracle.BVH(*c["B"], K_DOP, BRANCH, BITS, TREELET)
+    per_step = args.cpu_sample or 64
+    P = c["poses"]
+    for w in range(args.warmup):
+        take = P[(w * per_step) % len(P):][:per_step]
+        oracle.collide(A, B, take)
+        oracle.distance(A, B, take)
+    times = []
+    for s in range(args.steps):
+        take = P[(s * per_step) % len(P):][:per_step]
+        t0 = time.perf_counter()
+        oracle.collide(A, B, take)
+        oracle.distance(A, B, take)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = 2 * per_step * args.steps / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pose queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "terrain 512x512 (524,288 tris) vs displaced level-5 icosphere (20,480 tris), "
+                               "24-DOP, branching 8, 8-bit deltas, 16 KB treelets",
+                   "poses_per_step": per_step, "sample": f"first {per_step} poses per step of the 10,000-pose set"},
+        "cpu_baseline": {"value": value, "unit": "pose queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{per_step} poses per step (CD with pairs + PQ), FP64 oracle, OpenMP over poses"},
+        "e2e": {"value": value, "unit": "pose queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,uuid")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = self.proc.communicate()[0]
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            if self.uuid and self.uuid not in f[7]:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ engine
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, local_rank, world = dist_env()
+    import torch
+    import paper_2012_05348_gb300 as cb
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    c = workload(args.poses, rank)
+    A = cb.BVH(*c["A"], K_DOP, BRANCH, BITS, TREELET, device=dev)
+    B = cb.BVH(*c["B"], K_DOP, BRANCH, BITS, TREELET, device=dev)
+    n = len(c["poses"])
+    poses_host = torch.from_numpy(c["poses"]).pin_memory()
+    poses = poses_host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = cb._stream_ptr(stream)
+    L = cb.lib
+    import ctypes as C
+
+    def P(t):
+        return C.c_void_p(t.data_ptr())
+
+    # size the pair buffer from a first run
+    first = cb.collide(A, B, poses)
+    cap = int(first.pairs.shape[0] * 1.25) + 1024
+    hit = torch.empty(n, dtype=torch.uint8, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    need = torch.zeros(1, dtype=torch.int64, device=dev)
+    dist_out = torch.empty(n, dtype=torch.float32, device=dev)
+    st_cd = torch.zeros(1, dtype=torch.int32, device=dev)
+    st_pq = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws_cd_b = cb.workspace_bytes(A, B, n, 0, cap)
+    ws_pq_b = cb.workspace_bytes(A, B, n, 1)
+    ws_cd = torch.empty(ws_cd_b, dtype=torch.uint8, device=dev)
+    ws_pq = torch.empty(ws_pq_b, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB of L2
+
+    def step(src):
+        rc = L.cbvh_collide(A.handle, B.handle, P(src), n, P(hit), P(off), P(pairs), cap, P(need), cb.SORT_PAIRS,
+                            P(ws_cd), ws_cd_b, P(st_cd), sp)
+        rc |= L.cbvh_distance(A.handle, B.handle, P(src), n, P(dist_out), P(ws_pq), ws_pq_b, P(st_pq), sp)
+        if rc:
+            raise cb.CbvhError(rc, L.cbvh_last_error().decode())
+
+    for _ in range(max(3, args.warmup)):
+        step(poses)
+    torch.cuda.synchronize()
+    if int(st_cd.item()) or int(st_pq.item()):
+        raise RuntimeError(f"device status {int(st_cd.item())} / {int(st_pq.item())}")
+    bv_cd, leaf_cd = cb.query_stats(ws_cd)
+    bv_pq, leaf_pq = cb.query_stats(ws_pq)
+    n_pairs = int(need.item())
+
+    # ---- timed: device-resident inputs; L2 flushed (untimed) before every step ----
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    kcd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    kpq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid or None) as clk:
+        for s in range(K):
+            flush.zero_()
+            ev[s][0].record(stream)
+            cb.profile_events(*kcd[s])
+            rc = L.cbvh_collide(A.handle, B.handle, P(poses), n, P(hit), P(off), P(pairs), cap, P(need),
+                                cb.SORT_PAIRS, P(ws_cd), ws_cd_b, P(st_cd), sp)
+            cb.profile_events(*kpq[s])
+            rc |= L.cbvh_distance(A.handle, B.handle, P(poses), n, P(dist_out), P(ws_pq), ws_pq_b, P(st_pq), sp)
+            cb.profile_events(None, None)
+            ev[s][1].record(stream)
+            if rc:
+                raise cb.CbvhError(rc, L.cbvh_last_error().decode())
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    cd_ms = [a.elapsed_time(b) for a, b in kcd]
+    pq_ms = [a.elapsed_time(b) for a, b in kpq]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = 2 * n * K * world / (total_ms / 1e3)
+
+    # ---- end to end: pinned host poses in, results out, every step ----
+    hit_h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    off_h = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    pairs_h = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
+    dist_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    poses_e = torch.empty_like(poses)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(K):
+        poses_e.copy_(poses_host, non_blocking=True)
+        step(poses_e)
+        hit_h.copy_(hit, non_blocking=True)
+        off_h.copy_(off, non_blocking=True)
+        pairs_h[:n_pairs].copy_(pairs[:n_pairs], non_blocking=True)
+        dist_h.copy_(dist_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_val = 2 * n * K * world / (e2e_ms / 1e3)
+    h2d = n * 48
+    d2h = n * 1 + (n + 1) * 8 + n_pairs * 8 + n * 4
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    # ---- roofline of the dominant kernel (the traversal, CD or PQ) ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    cd_bytes = bv_cd * BYTES_BV + leaf_cd * BYTES_LEAF + n * BYTES_POSE + n_pairs * 3 * 4
+    pq_bytes = bv_pq * BYTES_BV + leaf_pq * BYTES_LEAF + n * BYTES_POSE
+    cd_avg, pq_avg = statistics.mean(cd_ms), statistics.mean(pq_ms)
+    dom = ("traverse_kernel<CD>", cd_bytes, cd_avg) if cd_avg >= pq_avg else ("traverse_kernel<PQ>", pq_bytes, pq_avg)
+    achieved = dom[1] / (dom[2] / 1e3) / 1e9
+    traffic = None
+    tr_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_file):
+        try:
+            traffic = json.load(open(tr_file)).get(dom[0])
+        except (OSError, ValueError):
+            traffic = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, done, secs, cores = oracle_rate(c, args.cpu_sample)
+        cpu = {"value": rate, "unit": "pose queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {done} poses of the 10,000-pose set, CD with pairs + PQ, {secs:.1f} s"}
+    sm = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": "pose queries/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "terrain 512x512 (524,288 tris) vs displaced level-5 icosphere (20,480 tris), "
+                               "24-DOP, branching 8, 8-bit deltas, 16 KB treelets",
+                   "poses": n, "step": "CD with sorted pair lists + PQ, every pose",
+                   "l2": "flushed (256 MB write, untimed) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "cd_pose_queries_per_s": n / (statistics.mean(cd_ms) / 1e3),
+        "pq_pose_queries_per_s": n / (statistics.mean(pq_ms) / 1e3),
+        "bv_pair_tests_per_s": (bv_cd + bv_pq) * K / (total_ms / 1e3),
+        "bv_pair_tests_per_step": bv_cd + bv_pq, "leaf_tests_per_step": leaf_cd + leaf_pq,
+        "pairs_per_step": n_pairs,
+        "latency_ms": {"p50": sm[len(sm) // 2], "p99": sm[min(len(sm) - 1, int(round(0.99 * (len(sm) - 1))))],
+                       "per": f"step of {n} poses (one CD + one PQ launch group)"},
+        "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} HBM copy bandwidth",
+                     "bytes": "algorithmic: BV tests x 34 B + leaf tests x 72 B + poses x 61 B (+ 12 B per pair)"},
+        "kernel_ms": {"traverse_cd": cd_avg, "traverse_pq": pq_avg},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "pose queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": K * 5,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/*
+ * cbvh.h -- C ABI of the GB300 engine for simultaneous traversal of two compressed k-DOP
+ * bounding volume hierarchies: collision detection (CD) and proximity query (PQ) over many
+ * rigid poses.  Method: Tan, Weller & Zachmann, "Compressed Bounding Volume Hierarchies for
+ * Collision Detection & Proximity Query" (arXiv 2012.05348), Algorithm 1 and Sec. III.
+ *
+ * Conventions
+ *   - Every call returns 0 (CBVH_OK) or a negative CBVH_ERR_* code and never throws.
+ *     cbvh_last_error() returns a thread-local message for the last failing call.
+ *   - Pointers are DEVICE pointers unless the parameter name ends in _host.
+ *   - The library never allocates device memory.  The caller owns every device buffer:
+ *     the BVH blob (cbvh_attach), outputs and a workspace sized by cbvh_workspace_bytes.
+ *     A cbvh_bvh handle owns only host memory.
+ *   - Query calls are asynchronous on the given cudaStream_t (a CUstream / cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).  Host-side argument errors are
+ *     returned at once.  Errors only known on the device (capacity, stack, timeout) are
+ *     written to the int32 device word `status` (0 = OK) that every query takes; read it
+ *     after synchronising the stream.
+ *   - Poses are n x 12 FP32, row-major: the rotation R (9 values) then the translation t
+ *     (3 values).  A pose maps a point of B into A's frame: x_A = R x_B + t.  R must be a
+ *     rotation (orthonormal up to FP32 rounding).
+ *   - Triangle indices in outputs are the caller's original triangle indices.
+ */
+#ifndef CBVH_H
+#define CBVH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CBVH_OK 0
+#define CBVH_ERR_ARG (-1)       /* invalid argument (k, branching, bits, treelet size, sizes, pointers) */
+#define CBVH_ERR_MESH (-2)      /* out-of-range index, degenerate triangle, non-finite or out-of-range coordinates */
+#define CBVH_ERR_CUDA (-3)      /* a CUDA runtime call failed; see cbvh_last_error() */
+#define CBVH_ERR_CAPACITY (-4)  /* device: more intersecting pairs than pair_capacity */
+#define CBVH_ERR_STACK (-5)     /* device: traversal stack bound exceeded (never by construction) */
+#define CBVH_ERR_TIMEOUT (-6)   /* device: a bounded wait or the traversal step cap ran out */
+#define CBVH_ERR_WORKSPACE (-7) /* workspace smaller than cbvh_workspace_bytes() */
+#define CBVH_ERR_STATE (-9)     /* handle has no device blob attached */
+
+/* collide flags */
+#define CBVH_EARLY_EXIT 1u /* stop each pose at its first intersecting pair (pair outputs must be NULL) */
+#define CBVH_SORT_PAIRS 2u /* sort each pose's pair list by (i, j) */
+
+typedef struct cbvh_bvh cbvh_bvh; /* opaque; immutable once built; concurrent reads are safe */
+
+typedef struct {
+  int64_t n_tris;
+  int64_t n_nodes;
+  int64_t n_treelets;
+  int64_t blob_bytes;   /* bytes of the device blob, triangles included */
+  int64_t node_bytes;   /* bytes of the treelets alone (the compressed hierarchy) */
+  int32_t k, branching, quant_bits, treelet_bytes;
+  int32_t lattice_exp;  /* e: lattice step 2^e */
+  int32_t depth;        /* tree depth (edges from the root to the deepest leaf) */
+  int32_t max_treelet_depth;
+  int32_t local_bits;   /* node reference = (treelet << local_bits) | local index */
+} cbvh_info_t;
+
+/* Last error message of the calling thread ("" if none). */
+const char *cbvh_last_error(void);
+
+/* Build the compressed BVH of a triangle mesh on the host.
+ *   verts_host: n_verts x 3 FP32; tris_host: n_tris x 3 int32 vertex indices.
+ *   k: 6, 18, 24 or 26 DOP values per node (Table 1: "k floats" per k-DOP); the k/2 slab
+ *      directions are fixed unnormalised integer vectors (axes, then edge diagonals, then
+ *      corner diagonals).
+ *   branching: 2, 4, 8 or 16 children per inner node; one triangle per leaf; each node is
+ *      split by log2(branching) rounds of median splits on the longest centroid axis.
+ *   quant_bits: 8 or 16 -- slab bounds quantised on one lattice of step 2^e ("we quantify
+ *      BV", abstract) and stored as predictor-corrector deltas (Sec. III-B): predictor =
+ *      the parent's decoded interval, corrector = outward b-bit delta; 0 -- uncompressed
+ *      FP32 bounds.
+ *   treelet_bytes: power of two in [4096, 131072]; the hierarchy is clustered into treelets
+ *      of at most this size (Sec. III-B), each with an absolute root for random access.
+ * On success *out receives a handle owning host memory only; attach a device copy of its
+ * blob with cbvh_attach before querying.  Errors: CBVH_ERR_ARG, CBVH_ERR_MESH. */
+int cbvh_build(const float *verts_host, int64_t n_verts, const int32_t *tris_host, int64_t n_tris, int k,
+               int branching, int quant_bits, int treelet_bytes, cbvh_bvh **out);
+
+/* Free a handle (host memory only; the attached device blob stays the caller's). */
+int cbvh_free(cbvh_bvh *h);
+
+int cbvh_info(const cbvh_bvh *h, cbvh_info_t *out);
+
+/* The host copy of the blob (read-only, owned by the handle, valid until cbvh_free). */
+int cbvh_blob_host(const cbvh_bvh *h, const uint8_t **blob_host, int64_t *bytes);
+
+/* Copy the blob into caller-owned device memory `dev_blob` (>= blob_bytes, 256-byte
+ * aligned) on `stream` and remember that address for queries.  The caller keeps the buffer
+ * alive and unchanged while the handle is used.  Errors: CBVH_ERR_ARG, CBVH_ERR_CUDA. */
+int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *stream);
+
+/* Test hook: decode every node on the device, in blob order (treelet by treelet, local
+ * index order).  lattice_out: n_nodes x (k/2) x 2 int32 decoded lattice bounds [lo, hi]
+ * (not written when quant_bits = 0; may be NULL); bounds_out: n_nodes x (k/2) x 2 FP32
+ * bounds (lo rounded down, hi rounded up).  Asynchronous on `stream`. */
+int cbvh_decode_all(const cbvh_bvh *h, int32_t *lattice_out, float *bounds_out, void *stream);
+
+/* Bytes of device workspace a query needs (16-byte aligned pointer, contents need not be
+ * initialised).  mode: 0 = collide, 1 = distance; pair_capacity is ignored for distance
+ * and for collide without pair outputs. */
+int cbvh_workspace_bytes(const cbvh_bvh *A, const cbvh_bvh *B, int64_t n_poses, int mode, int64_t pair_capacity,
+                         int64_t *bytes);
+
+/* Collision detection, Algorithm 1 with checkPrimitives = closed triangle-triangle
+ * intersection, for n poses of B against A.
+ *   poses: n x 12 FP32.  hit: n bytes, 1 if any triangle of A meets a triangle of R B + t.
+ *   pair_offsets (n + 1 int64) and pairs (2 x pair_capacity int32, (i, j) = (triangle of A,
+ *   triangle of B)): the per-pose intersecting pairs in CSR form, or both NULL.
+ *   pairs_needed: device int64 scalar receiving the total number of pairs (may be NULL
+ *   when pairs are not requested).  If it exceeds pair_capacity, hit and pair_offsets are
+ *   still written, pairs is not, and `status` reads CBVH_ERR_CAPACITY: reallocate and call
+ *   again.  flags: CBVH_EARLY_EXIT, CBVH_SORT_PAIRS. */
+int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, uint8_t *hit,
+                 int64_t *pair_offsets, int32_t *pairs, int64_t pair_capacity, int64_t *pairs_needed, uint32_t flags,
+                 void *workspace, int64_t workspace_bytes, int32_t *status, void *stream);
+
+/* Proximity query: dist[p] = minimum distance between the triangles of A and those of
+ * R_p B + t_p (0 when they intersect), by branch-and-bound Algorithm 1 with slab-gap lower
+ * bounds.  FP32; accurate to a few ulps of the scene size. */
+int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist, void *workspace,
+                  int64_t workspace_bytes, int32_t *status, void *stream);
+
+/* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests
+ * (bounding-volume overlap or lower-bound tests, Algorithm 1's "a and b intersect"),
+ * stats_host[1] = leaf tests (checkPrimitives calls).  Copies 16 bytes to the host and
+ * synchronises `stream`.  The paper has no such call; it feeds the BV-pair tests/s metric. */
+int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream);
+
+/* Profiling: when both are non-NULL, every later query on this host thread records the
+ * CUDA event `before` immediately before its traversal kernel and `after` immediately after
+ * it, on the query's stream, so that the traversal kernel can be timed alone.  NULL, NULL
+ * turns it off.  Events are cudaEvent_t handles created by the caller. */
+int cbvh_profile_events(void *before, void *after);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBVH_H */

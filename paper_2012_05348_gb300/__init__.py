@@ -1,0 +1,234 @@
+"""Python binding of libcbvh, the GB300 engine for compressed k-DOP BVH collision detection
+(CD) and proximity query (PQ) -- Tan, Weller & Zachmann, arXiv 2012.05348, Algorithm 1.
+
+Argument marshalling only: every step of a query runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  The functions mirror the C ABI in
+include/cbvh.h (cbvh_build, cbvh_collide, cbvh_distance, ...).
+
+Importing fails loudly when libcbvh.so has not been built (``__graft_entry__.build()`` or
+``python -m paper_2012_05348_gb300._build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["BVH", "collide", "distance", "workspace_bytes", "query_stats", "profile_events", "CbvhError", "lib",
+           "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
+
+LIB_PATH = _build.LIB
+EARLY_EXIT = 1
+SORT_PAIRS = 2
+ERR = {0: "OK", -1: "ARG", -2: "MESH", -3: "CUDA", -4: "CAPACITY", -5: "STACK", -6: "TIMEOUT", -7: "WORKSPACE",
+       -9: "STATE"}
+
+
+
+class _Info(C.Structure):
+    _fields_ = [("n_tris", C.c_int64), ("n_nodes", C.c_int64), ("n_treelets", C.c_int64),
+                ("blob_bytes", C.c_int64), ("node_bytes", C.c_int64), ("k", C.c_int32), ("branching", C.c_int32),
+                ("quant_bits", C.c_int32), ("treelet_bytes", C.c_int32), ("lattice_exp", C.c_int32),
+                ("depth", C.c_int32), ("max_treelet_depth", C.c_int32), ("local_bits", C.c_int32)]
+
+
+def _declare(L):
+    P, I64, I32, U32 = C.c_void_p, C.c_int64, C.c_int, C.c_uint32
+    L.cbvh_last_error.restype = C.c_char_p
+    L.cbvh_build.argtypes = [P, I64, P, I64, I32, I32, I32, I32, C.POINTER(P)]
+    L.cbvh_free.argtypes = [P]
+    L.cbvh_info.argtypes = [P, C.POINTER(_Info)]
+    L.cbvh_blob_host.argtypes = [P, C.POINTER(P), C.POINTER(I64)]
+    L.cbvh_attach.argtypes = [P, P, I64, P]
+    L.cbvh_decode_all.argtypes = [P, P, P, P]
+    L.cbvh_workspace_bytes.argtypes = [P, P, I64, I32, I64, C.POINTER(I64)]
+    L.cbvh_collide.argtypes = [P, P, P, I64, P, P, P, I64, P, U32, P, I64, P, P]
+    L.cbvh_distance.argtypes = [P, P, P, I64, P, P, I64, P, P]
+    L.cbvh_query_stats.argtypes = [P, P, P]
+    L.cbvh_profile_events.argtypes = [P, P]
+    for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
+              "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_events"):
+        getattr(L, f).restype = I32
+    return L
+
+
+_lib = None
+
+
+def _load():
+    """Load libcbvh.so once; raise if it has not been built (there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2012_05348_gb300._build` "
+                              "(the engine has no CPU fallback)")
+        _lib = _declare(C.CDLL(LIB_PATH))
+    return _lib
+
+
+def __getattr__(name):
+    if name == "lib":
+        return _load()
+    raise AttributeError(name)
+
+
+class CbvhError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"cbvh error {code} ({ERR.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise CbvhError(rc, _load().cbvh_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+class BVH:
+    """A compressed k-DOP BVH: built on the host by cbvh_build, blob resident on the device
+    in a torch-allocated buffer attached with cbvh_attach."""
+
+    def __init__(self, verts, tris, k: int = 18, branching: int = 4, quant_bits: int = 16,
+                 treelet_bytes: int = 4096, device="cuda"):
+        v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+        t = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+        h = C.c_void_p()
+        _check(_load().cbvh_build(v.ctypes.data_as(C.c_void_p), len(v), t.ctypes.data_as(C.c_void_p), len(t), k,
+                              branching, quant_bits, treelet_bytes, C.byref(h)))
+        self._h = h
+        info = _Info()
+        _check(_load().cbvh_info(h, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
+        self.blob_dev = None
+        if device is not None:
+            self.attach(device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def blob_host(self) -> np.ndarray:
+        p, n = C.c_void_p(), C.c_int64()
+        _check(_load().cbvh_blob_host(self._h, C.byref(p), C.byref(n)))
+        return np.ctypeslib.as_array((C.c_uint8 * n.value).from_address(p.value)).copy()
+
+    def attach(self, device="cuda", stream=None):
+        torch = _torch()
+        n = self.info["blob_bytes"]
+        self.blob_dev = torch.empty(n, dtype=torch.uint8, device=device)
+        with torch.cuda.device(self.blob_dev.device):
+            _check(_load().cbvh_attach(self._h, _ptr(self.blob_dev), n, _stream_ptr(stream)))
+
+    def decode_all(self, stream=None):
+        """(lattice int32 (n, K, 2) or None, bounds float32 (n, K, 2)) on the device, blob order."""
+        torch = _torch()
+        n, K = self.info["n_nodes"], self.info["k"] // 2
+        dev = self.blob_dev.device
+        lat = torch.empty((n, K, 2), dtype=torch.int32, device=dev) if self.info["quant_bits"] else None
+        f = torch.empty((n, K, 2), dtype=torch.float32, device=dev)
+        _check(_load().cbvh_decode_all(self._h, _ptr(lat), _ptr(f), _stream_ptr(stream)))
+        return lat, f
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().cbvh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def workspace_bytes(A: BVH, B: BVH, n: int, mode: int, pair_capacity: int = 0) -> int:
+    out = C.c_int64()
+    _check(_load().cbvh_workspace_bytes(A.handle, B.handle, n, mode, pair_capacity, C.byref(out)))
+    return out.value
+
+
+@dataclass
+class CollideResult:
+    hit: object          # uint8 (n,)
+    offsets: object      # int64 (n + 1,) or None
+    pairs: object        # int32 (P, 2) or None
+    status: int
+
+
+def collide(A: BVH, B: BVH, poses, *, pairs: bool = True, sort: bool = True, early_exit: bool = False,
+            capacity: int | None = None, stream=None, out=None, check: bool = True) -> CollideResult:
+    """cbvh_collide on device poses (n, 12) float32.  With ``pairs`` the per-pose intersecting
+    triangle pairs come back in CSR form; if the capacity is exceeded the call is repeated
+    once with the exact size the device reported."""
+    torch = _torch()
+    n = int(poses.shape[0])
+    dev = poses.device
+    flags = (EARLY_EXIT if early_exit else 0) | (SORT_PAIRS if (pairs and sort) else 0)
+    st = _stream_ptr(stream)
+    cap = int(capacity if capacity is not None else max(1024, 16 * n)) if pairs else 0
+    for _attempt in range(2):
+        hit = torch.empty(n, dtype=torch.uint8, device=dev)
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev) if pairs else None
+        prs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev) if pairs else None
+        need = torch.zeros(1, dtype=torch.int64, device=dev) if pairs else None
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        wsb = workspace_bytes(A, B, n, 0, cap)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        _check(_load().cbvh_collide(A.handle, B.handle, _ptr(poses), n, _ptr(hit), _ptr(off), _ptr(prs), cap, _ptr(need),
+                                flags, _ptr(ws), wsb, _ptr(status), st))
+        code = int(status.item())
+        if code == -4 and pairs:
+            cap = int(need.item())
+            continue
+        if check and code != 0:
+            raise CbvhError(code, "device status")
+        total = int(need.item()) if pairs else 0
+        return CollideResult(hit, off, prs[:total] if pairs else None, code)
+    raise CbvhError(-4, "pair capacity still exceeded after resizing")
+
+
+def query_stats(workspace, stream=None):
+    """(BV-pair tests, leaf tests) of the last query that used this workspace tensor."""
+    out = np.zeros(2, np.int64)
+    _check(_load().cbvh_query_stats(_ptr(workspace), out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+    return int(out[0]), int(out[1])
+
+
+def profile_events(before=None, after=None):
+    """Record torch.cuda.Event `before` / `after` around every later traversal launch."""
+    b = C.c_void_p(before.cuda_event) if before is not None else C.c_void_p(0)
+    a = C.c_void_p(after.cuda_event) if after is not None else C.c_void_p(0)
+    _check(_load().cbvh_profile_events(b, a))
+
+
+def distance(A: BVH, B: BVH, poses, *, stream=None, check: bool = True):
+    """cbvh_distance on device poses (n, 12) float32 -> float32 (n,)."""
+    torch = _torch()
+    n = int(poses.shape[0])
+    dev = poses.device
+    dist = torch.empty(n, dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    wsb = workspace_bytes(A, B, n, 1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    _check(_load().cbvh_distance(A.handle, B.handle, _ptr(poses), n, _ptr(dist), _ptr(ws), wsb, _ptr(status),
+                             _stream_ptr(stream)))
+    if check:
+        code = int(status.item())
+        if code != 0:
+            raise CbvhError(code, "device status")
+    return dist

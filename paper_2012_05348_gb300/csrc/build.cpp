@@ -1,0 +1,536 @@
+// Host-side BVH builder and treelet encoder of libcbvh.
+//
+// Produces the compressed blob that the CUDA kernels traverse:
+//   * k-DOP bounding volumes over k/2 fixed integer directions (Table 1: "k floats" per
+//     k-DOP), one triangle per leaf, `branching` children per inner node;
+//   * bounds quantised on one absolute lattice of step 2^e ("we quantify BV", abstract):
+//     lo = floor(d.v / 2^e), hi = ceil(d.v / 2^e) of the exact real products;
+//   * predictor-corrector deltas (abstract; Sec. III-B, "predictors based on the delta to
+//     the parent nodes"): a node is predicted by its parent's decoded interval and
+//     corrected by b-bit unsigned deltas that round outward;
+//   * treelets (Sec. III-B, "clustering BVHs into a smaller parts"): greedy breadth-first
+//     clusters of whole sibling groups within a byte budget, each with an absolute root so
+//     that any treelet is randomly accessible (abstract).
+//
+// Blob layout (little endian; offsets from the blob start):
+//   [0, 64)     header: magic 'CBVH', version, k, K, m, bits, lbits, max treelet depth,
+//               e, n_tris, n_nodes, n_treelets, record bytes, root record bytes, treelet
+//               budget, tree depth, 0, offset of the triangle table, total bytes
+//   [64, ...)   u64 treelet offsets [n_treelets + 1]
+//   treelets    16-byte aligned: {u32 node count, u32 blob-order index of the root, 0, 0},
+//               the root record, then fixed-size records in treelet BFS order
+//   triangles   48 bytes per leaf, in leaf order: v0.xyz, original index, v1.xyz, 0, v2.xyz, 0
+// Record: u32 w0 = parent local index (0xFFFF at the root) | child count << 16 |
+//         children-are-treelet-roots << 21 | depth below the treelet root << 24;
+//         u32 w1 = first child (local index, or treelet id when external) or, at a leaf,
+//         its leaf-order triangle slot; then per direction j the pair (lo, hi): absolute
+//         int32 lattice values at a treelet root, b-bit correctors elsewhere, or FP32
+//         values (lo rounded down, hi rounded up) everywhere when quant_bits = 0.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <limits>
+#include <numeric>
+
+#include "internal.h"
+
+namespace {
+
+// Slab directions; the k-DOP uses the first k/2.
+const int kDir[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
+                         {0, 1, 1},  {0, 1, -1}, {1, 1, 1},  {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
+
+// ---------------------------------------------------------------- exact lattice rounding
+// Exact floor of a + b + c.  Fast path: the rounded sum is far enough from an integer
+// that its rounding error (at most 2u (|a| + |b| + |c|)) cannot cross one.  Otherwise the
+// sum is turned into a non-overlapping expansion (Knuth's TwoSum, Shewchuk's
+// Grow-Expansion) and its floor is read from the largest component down.
+inline void two_sum(double a, double b, double &s, double &err) {
+  s = a + b;
+  double bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+}
+
+int64_t exact_floor(double a, double b, double c) {
+  double s = (a + b) + c;
+  double slack = 4.0 * std::ldexp(std::fabs(a) + std::fabs(b) + std::fabs(c), -53);
+  double f1 = std::floor(s - slack), f2 = std::floor(s + slack);
+  if (f1 == f2) return (int64_t)f1;
+  double x, ex, y, ey;
+  two_sum(a, b, x, ex);
+  two_sum(c, ex, y, ey);
+  double z, ez;
+  two_sum(y, x, z, ez);
+  double comp[3] = {z, ez, ey};  // largest first
+  int64_t acc = 0;
+  for (double v : comp) {
+    double fl = std::floor(v);
+    if (fl != v) return acc + (int64_t)fl;
+    acc += (int64_t)v;
+  }
+  return acc;
+}
+inline int64_t exact_ceil(double a, double b, double c) { return -exact_floor(-a, -b, -c); }
+
+// RD / RU conversion of a lattice integer to FP32, then exact scaling by 2^e.
+float to_f32_down(int64_t L, int e) {
+  float f = (float)L;
+  if ((double)f > (double)L) f = std::nextafter(f, -std::numeric_limits<float>::infinity());
+  return std::ldexp(f, e);
+}
+float to_f32_up(int64_t L, int e) {
+  float f = (float)L;
+  if ((double)f < (double)L) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+  return std::ldexp(f, e);
+}
+
+struct Node {
+  int32_t parent = -1, first = -1, count = 0, tri = -1, depth = 0;
+};
+
+struct Builder {
+  int k, K, m, bits, budget;
+  const float *V;
+  int64_t nv;
+  const int32_t *T;
+  int64_t nt;
+  std::vector<double> key;  // nt x 3
+  std::vector<Node> nodes;  // BFS order
+  std::vector<int32_t> perm;
+  int e = 0;
+  std::vector<int32_t> vlat;  // per vertex, per direction: lo, hi
+  std::vector<int32_t> lat;   // per node, per direction: lo, hi (exact)
+
+  // Partition perm[s, s+n) so that its first n/2 entries are the n/2 smallest by
+  // (centroid key on the axis of largest centroid extent, triangle index).
+  void split(int64_t s, int64_t n) {
+    double lo[3], hi[3];
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::numeric_limits<double>::infinity();
+      hi[c] = -lo[c];
+    }
+    for (int64_t i = s; i < s + n; ++i)
+      for (int c = 0; c < 3; ++c) {
+        double v = key[3 * (int64_t)perm[i] + c];
+        lo[c] = std::min(lo[c], v);
+        hi[c] = std::max(hi[c], v);
+      }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+      if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
+    const double *kp = key.data();
+    std::nth_element(perm.begin() + s, perm.begin() + s + n / 2, perm.begin() + s + n, [kp, ax](int32_t a, int32_t b) {
+      double ka = kp[3 * (int64_t)a + ax], kb = kp[3 * (int64_t)b + ax];
+      return ka < kb || (ka == kb && a < b);
+    });
+  }
+
+  void build_tree() {
+    perm.resize(nt);
+    std::iota(perm.begin(), perm.end(), 0);
+    struct Item {
+      int32_t node;
+      int64_t s, n;
+    };
+    std::deque<Item> q;
+    nodes.reserve(2 * nt);
+    nodes.emplace_back();
+    q.push_back({0, 0, nt});
+    while (!q.empty()) {
+      Item it = q.front();
+      q.pop_front();
+      if (it.n == 1) {
+        nodes[it.node].tri = perm[it.s];
+        continue;
+      }
+      std::vector<std::pair<int64_t, int64_t>> groups{{it.s, it.n}};
+      for (int r = 1; r < m; r <<= 1) {
+        std::vector<std::pair<int64_t, int64_t>> next;
+        for (auto [s, n] : groups) {
+          if (n == 1) {
+            next.push_back({s, 1});
+            continue;
+          }
+          split(s, n);
+          next.push_back({s, n / 2});
+          next.push_back({s + n / 2, n - n / 2});
+        }
+        groups.swap(next);
+      }
+      int32_t first = (int32_t)nodes.size();
+      nodes[it.node].first = first;
+      nodes[it.node].count = (int32_t)groups.size();
+      for (auto [s, n] : groups) {
+        Node c;
+        c.parent = it.node;
+        c.depth = nodes[it.node].depth + 1;
+        nodes.push_back(c);
+        q.push_back({(int32_t)nodes.size() - 1, s, n});
+      }
+    }
+  }
+
+  // true when every |d.v| / 2^e < 2^30
+  bool fits(int ex) const {
+    const int64_t L = int64_t(1) << 30;
+    for (int64_t v = 0; v < nv; ++v)
+      for (int j = 0; j < K; ++j) {
+        double t[3];
+        for (int c = 0; c < 3; ++c) t[c] = kDir[j][c] * std::ldexp((double)V[3 * v + c], -ex);
+        if (exact_floor(t[0], t[1], t[2]) > L - 1 || exact_ceil(t[0], t[1], t[2]) < -(L - 1)) return false;
+      }
+    return true;
+  }
+};
+
+uint32_t f32_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+void w32(std::vector<uint8_t> &b, int64_t o, uint32_t v) { std::memcpy(&b[o], &v, 4); }
+void w64(std::vector<uint8_t> &b, int64_t o, uint64_t v) { std::memcpy(&b[o], &v, 8); }
+void w16(std::vector<uint8_t> &b, int64_t o, uint16_t v) { std::memcpy(&b[o], &v, 2); }
+
+}  // namespace
+
+extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_t *tris_host, int64_t n_tris, int k,
+                          int branching, int quant_bits, int treelet_bytes, cbvh_bvh **out) {
+  cbvh::clear_error();
+  if (!out) return cbvh::fail(CBVH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!verts_host || !tris_host) return cbvh::fail(CBVH_ERR_ARG, "NULL mesh pointer");
+  if (k != 6 && k != 18 && k != 24 && k != 26) return cbvh::fail(CBVH_ERR_ARG, "k must be 6, 18, 24 or 26");
+  if (branching != 2 && branching != 4 && branching != 8 && branching != 16)
+    return cbvh::fail(CBVH_ERR_ARG, "branching must be 2, 4, 8 or 16");
+  if (quant_bits != 0 && quant_bits != 8 && quant_bits != 16)
+    return cbvh::fail(CBVH_ERR_ARG, "quant_bits must be 0, 8 or 16");
+  if (treelet_bytes < 4096 || treelet_bytes > 131072 || (treelet_bytes & (treelet_bytes - 1)))
+    return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes must be a power of two in [4096, 131072]");
+  if (n_tris < 1 || n_tris > 0x7fffffff || n_verts < 3 || n_verts > 0x7fffffff)
+    return cbvh::fail(CBVH_ERR_MESH, "mesh size out of range");
+
+  auto h = new cbvh_bvh();
+  h->k = k;
+  h->K = k / 2;
+  h->m = branching;
+  h->bits = quant_bits;
+  h->treelet_bytes = treelet_bytes;
+  const int K = h->K;
+  h->root_bytes = 8 + 8 * K;
+  h->rec_bytes = quant_bits == 0 ? h->root_bytes : (8 + 2 * K * (quant_bits / 8) + 3) / 4 * 4;
+  if (16 + h->root_bytes + branching * h->rec_bytes > treelet_bytes) {
+    delete h;
+    return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes too small for one sibling group");
+  }
+
+  Builder B{k, K, branching, quant_bits, treelet_bytes, verts_host, n_verts, tris_host, n_tris};
+  for (int64_t i = 0; i < 3 * n_verts; ++i)
+    if (!std::isfinite(verts_host[i])) {
+      delete h;
+      return cbvh::fail(CBVH_ERR_MESH, "non-finite vertex coordinate");
+    }
+  B.key.resize(3 * n_tris);
+  for (int64_t t = 0; t < n_tris; ++t) {
+    double p[3][3];
+    for (int c = 0; c < 3; ++c) {
+      int32_t vi = tris_host[3 * t + c];
+      if (vi < 0 || vi >= n_verts) {
+        delete h;
+        return cbvh::fail(CBVH_ERR_MESH, "triangle " + std::to_string(t) + " has an out-of-range vertex index");
+      }
+      for (int x = 0; x < 3; ++x) p[c][x] = verts_host[3 * (int64_t)vi + x];
+    }
+    double a[3], b[3];
+    for (int x = 0; x < 3; ++x) {
+      a[x] = p[1][x] - p[0][x];
+      b[x] = p[2][x] - p[0][x];
+    }
+    double nx = a[1] * b[2] - a[2] * b[1], ny = a[2] * b[0] - a[0] * b[2], nz = a[0] * b[1] - a[1] * b[0];
+    if (nx == 0.0 && ny == 0.0 && nz == 0.0) {
+      delete h;
+      return cbvh::fail(CBVH_ERR_MESH, "triangle " + std::to_string(t) + " is degenerate (zero area)");
+    }
+    for (int x = 0; x < 3; ++x) B.key[3 * t + x] = (p[0][x] + p[1][x]) + p[2][x];
+  }
+  B.build_tree();
+  const int64_t nn = (int64_t)B.nodes.size();
+
+  // Lattice exponent: the smallest e with |d.v| / 2^e < 2^30 over the referenced vertices.
+  // Unreferenced vertices must not influence it: restrict to vertices used by a triangle.
+  std::vector<uint8_t> used(n_verts, 0);
+  for (int64_t i = 0; i < 3 * n_tris; ++i) used[tris_host[i]] = 1;
+  std::vector<float> UV;
+  std::vector<int64_t> vmap(n_verts, -1);
+  for (int64_t v = 0; v < n_verts; ++v)
+    if (used[v]) {
+      vmap[v] = (int64_t)UV.size() / 3;
+      UV.insert(UV.end(), verts_host + 3 * v, verts_host + 3 * v + 3);
+    }
+  Builder E = B;
+  E.V = UV.data();
+  E.nv = (int64_t)UV.size() / 3;
+  {
+    double M = 0;
+    for (int64_t v = 0; v < E.nv; ++v)
+      for (int j = 0; j < K; ++j) {
+        double s = kDir[j][0] * (double)UV[3 * v] + kDir[j][1] * (double)UV[3 * v + 1] + kDir[j][2] * (double)UV[3 * v + 2];
+        M = std::max(M, std::fabs(s));
+      }
+    if (M == 0.0) {
+      delete h;
+      return cbvh::fail(CBVH_ERR_MESH, "mesh has no extent");
+    }
+    int ex = std::ilogb(M) - 29;  // 2^(ilogb M + 1) > M: fits unless rounding says otherwise
+    while (!E.fits(ex)) ++ex;
+    while (E.fits(ex - 1)) --ex;
+    if (ex < -120 || ex > 96) {
+      delete h;
+      return cbvh::fail(CBVH_ERR_MESH, "mesh coordinates outside the supported range");
+    }
+    h->e = ex;
+  }
+  // per-vertex lattice values, then node bounds bottom-up (children follow parents in BFS)
+  std::vector<int32_t> vl((size_t)E.nv * K * 2);
+  for (int64_t v = 0; v < E.nv; ++v)
+    for (int j = 0; j < K; ++j) {
+      double t[3];
+      for (int c = 0; c < 3; ++c) t[c] = kDir[j][c] * std::ldexp((double)UV[3 * v + c], -h->e);
+      vl[(v * K + j) * 2] = (int32_t)exact_floor(t[0], t[1], t[2]);
+      vl[(v * K + j) * 2 + 1] = (int32_t)exact_ceil(t[0], t[1], t[2]);
+    }
+  std::vector<int32_t> lat((size_t)nn * K * 2);
+  for (int64_t x = nn - 1; x >= 0; --x) {
+    int32_t *L = &lat[(size_t)x * K * 2];
+    for (int j = 0; j < K; ++j) {
+      L[2 * j] = std::numeric_limits<int32_t>::max();
+      L[2 * j + 1] = std::numeric_limits<int32_t>::min();
+    }
+    const Node &nd = B.nodes[x];
+    if (nd.count == 0) {
+      for (int c = 0; c < 3; ++c) {
+        const int32_t *P = &vl[(size_t)vmap[tris_host[3 * (int64_t)nd.tri + c]] * K * 2];
+        for (int j = 0; j < K; ++j) {
+          L[2 * j] = std::min(L[2 * j], P[2 * j]);
+          L[2 * j + 1] = std::max(L[2 * j + 1], P[2 * j + 1]);
+        }
+      }
+    } else {
+      for (int c = 0; c < nd.count; ++c) {
+        const int32_t *P = &lat[(size_t)(nd.first + c) * K * 2];
+        for (int j = 0; j < K; ++j) {
+          L[2 * j] = std::min(L[2 * j], P[2 * j]);
+          L[2 * j + 1] = std::max(L[2 * j + 1], P[2 * j + 1]);
+        }
+      }
+    }
+  }
+  for (const Node &nd : B.nodes) h->depth = std::max(h->depth, nd.depth);
+
+  // ---- treelets: greedy BFS of whole sibling groups inside the byte budget ----
+  std::vector<int32_t> tlet(nn), local(nn), child_tlet(nn, -1);
+  std::vector<uint8_t> ext(nn, 0);
+  std::vector<int32_t> roots{0};
+  std::vector<std::vector<int32_t>> members;
+  for (size_t t = 0; t < roots.size(); ++t) {
+    std::vector<int32_t> mem{roots[t]};
+    tlet[roots[t]] = (int32_t)t;
+    local[roots[t]] = 0;
+    int64_t used_bytes = 16 + h->root_bytes;
+    for (size_t i = 0; i < mem.size(); ++i) {  // `mem` doubles as the BFS queue
+      const Node &nd = B.nodes[mem[i]];
+      if (nd.count == 0) continue;
+      int64_t need = (int64_t)nd.count * h->rec_bytes;
+      if (used_bytes + need <= treelet_bytes) {
+        used_bytes += need;
+        for (int c = 0; c < nd.count; ++c) {
+          tlet[nd.first + c] = (int32_t)t;
+          local[nd.first + c] = (int32_t)mem.size();
+          mem.push_back(nd.first + c);
+        }
+      } else {
+        ext[mem[i]] = 1;
+        child_tlet[mem[i]] = (int32_t)roots.size();
+        for (int c = 0; c < nd.count; ++c) roots.push_back(nd.first + c);
+      }
+    }
+    members.push_back(std::move(mem));
+  }
+  const int64_t ntl = (int64_t)roots.size();
+  size_t maxn = 1;
+  for (auto &mm : members) maxn = std::max(maxn, mm.size());
+  if (maxn > 65535) {
+    delete h;
+    return cbvh::fail(CBVH_ERR_ARG, "too many nodes in one treelet");
+  }
+  while (((size_t)1 << h->lbits) < maxn) ++h->lbits;
+  if (h->lbits < 32 && (uint64_t)ntl >= ((uint64_t)1 << (32 - h->lbits))) {
+    delete h;
+    return cbvh::fail(CBVH_ERR_ARG, "too many treelets for 32-bit node references; use larger treelets");
+  }
+
+  // ---- predictor-corrector encoding, top-down (parents precede children in BFS) ----
+  std::vector<int32_t> dec((size_t)nn * K * 2);
+  std::vector<uint16_t> corr((size_t)nn * K * 2, 0);
+  const uint32_t dmax = quant_bits ? (1u << quant_bits) - 1 : 0;
+  for (int64_t x = 0; x < nn; ++x) {
+    const int32_t *C = &lat[(size_t)x * K * 2];
+    int32_t *D = &dec[(size_t)x * K * 2];
+    if (local[x] == 0 || quant_bits == 0) {
+      std::copy(C, C + 2 * K, D);
+      continue;
+    }
+    const int32_t *P = &dec[(size_t)B.nodes[x].parent * K * 2];
+    for (int j = 0; j < K; ++j) {
+      uint32_t range = (uint32_t)((int64_t)P[2 * j + 1] - P[2 * j]);
+      int s = 0;
+      while ((range >> s) > dmax) ++s;
+      uint32_t dl = (uint32_t)((int64_t)C[2 * j] - P[2 * j]) >> s;
+      uint32_t dh = (uint32_t)((int64_t)P[2 * j + 1] - C[2 * j + 1]) >> s;
+      corr[(size_t)x * K * 2 + 2 * j] = (uint16_t)dl;
+      corr[(size_t)x * K * 2 + 2 * j + 1] = (uint16_t)dh;
+      D[2 * j] = (int32_t)((int64_t)P[2 * j] + ((int64_t)dl << s));
+      D[2 * j + 1] = (int32_t)((int64_t)P[2 * j + 1] - ((int64_t)dh << s));
+    }
+  }
+
+  // ---- serialise ----
+  std::vector<int64_t> toff(ntl + 1);
+  int64_t pos = (64 + 8 * (ntl + 1) + 15) / 16 * 16;
+  h->off_treelets = pos;
+  for (int64_t t = 0; t < ntl; ++t) {
+    toff[t] = pos;
+    pos += (16 + h->root_bytes + (int64_t)(members[t].size() - 1) * h->rec_bytes + 15) / 16 * 16;
+  }
+  toff[ntl] = pos;
+  h->off_tris = pos;
+  const int64_t total = pos + 48 * n_tris;
+  std::vector<uint8_t> &b = h->blob;
+  b.assign(total, 0);
+  int max_td = 0;
+  std::vector<int32_t> leaf_slot(nn, -1), slot_tri;
+  slot_tri.reserve(n_tris);
+  for (int64_t x = 0; x < nn; ++x)
+    if (B.nodes[x].count == 0) {
+      leaf_slot[x] = (int32_t)slot_tri.size();
+      slot_tri.push_back(B.nodes[x].tri);
+    }
+  int64_t first_node = 0;
+  for (int64_t t = 0; t < ntl; ++t) {
+    const auto &mem = members[t];
+    const int64_t T0 = toff[t];
+    w32(b, T0, (uint32_t)mem.size());
+    w32(b, T0 + 4, (uint32_t)first_node);
+    first_node += (int64_t)mem.size();
+    std::vector<int> tdepth(mem.size(), 0);
+    for (size_t l = 0; l < mem.size(); ++l) {
+      const int32_t x = mem[l];
+      const Node &nd = B.nodes[x];
+      if (l) tdepth[l] = tdepth[local[nd.parent]] + 1;
+      max_td = std::max(max_td, tdepth[l]);
+      const int64_t R = T0 + 16 + (l ? h->root_bytes + (int64_t)(l - 1) * h->rec_bytes : 0);
+      uint32_t w0 = (l ? (uint32_t)local[nd.parent] : 0xFFFFu) | ((uint32_t)nd.count << 16) |
+                    ((uint32_t)ext[x] << 21) | ((uint32_t)tdepth[l] << 24);
+      uint32_t w1 = nd.count == 0 ? (uint32_t)leaf_slot[x]
+                                  : (ext[x] ? (uint32_t)child_tlet[x] : (uint32_t)local[nd.first]);
+      w32(b, R, w0);
+      w32(b, R + 4, w1);
+      const int32_t *D = &dec[(size_t)x * K * 2];
+      for (int j = 0; j < K; ++j) {
+        if (quant_bits == 0) {
+          w32(b, R + 8 + 8 * j, f32_bits(to_f32_down(D[2 * j], h->e)));
+          w32(b, R + 12 + 8 * j, f32_bits(to_f32_up(D[2 * j + 1], h->e)));
+        } else if (l == 0) {
+          w32(b, R + 8 + 8 * j, (uint32_t)D[2 * j]);
+          w32(b, R + 12 + 8 * j, (uint32_t)D[2 * j + 1]);
+        } else if (quant_bits == 8) {
+          b[R + 8 + 2 * j] = (uint8_t)corr[(size_t)x * K * 2 + 2 * j];
+          b[R + 9 + 2 * j] = (uint8_t)corr[(size_t)x * K * 2 + 2 * j + 1];
+        } else {
+          w16(b, R + 8 + 4 * j, corr[(size_t)x * K * 2 + 2 * j]);
+          w16(b, R + 10 + 4 * j, corr[(size_t)x * K * 2 + 2 * j + 1]);
+        }
+      }
+    }
+  }
+  for (int64_t i = 0; i < n_tris; ++i) {
+    const int64_t P = h->off_tris + 48 * i;
+    const int32_t t = slot_tri[i];
+    for (int c = 0; c < 3; ++c)
+      for (int x = 0; x < 3; ++x) w32(b, P + 16 * c + 4 * x, f32_bits(verts_host[3 * (int64_t)tris_host[3 * (int64_t)t + c] + x]));
+    w32(b, P + 12, (uint32_t)t);
+  }
+  h->max_tdepth = max_td;
+  h->n_tris = n_tris;
+  h->n_nodes = nn;
+  h->n_treelets = ntl;
+  // header
+  w32(b, 0, 0x48564243u);
+  w16(b, 4, 1);
+  b[6] = (uint8_t)k;
+  b[7] = (uint8_t)K;
+  b[8] = (uint8_t)branching;
+  b[9] = (uint8_t)quant_bits;
+  b[10] = (uint8_t)h->lbits;
+  b[11] = (uint8_t)max_td;
+  w32(b, 12, (uint32_t)h->e);
+  w32(b, 16, (uint32_t)n_tris);
+  w32(b, 20, (uint32_t)nn);
+  w32(b, 24, (uint32_t)ntl);
+  w32(b, 28, (uint32_t)h->rec_bytes);
+  w32(b, 32, (uint32_t)h->root_bytes);
+  w32(b, 36, (uint32_t)treelet_bytes);
+  w32(b, 40, (uint32_t)h->depth);
+  w32(b, 44, 0);
+  w64(b, 48, (uint64_t)h->off_tris);
+  w64(b, 56, (uint64_t)total);
+  for (int64_t t = 0; t <= ntl; ++t) w64(b, 64 + 8 * t, (uint64_t)toff[t]);
+  *out = h;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_free(cbvh_bvh *h) {
+  delete h;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_info(const cbvh_bvh *h, cbvh_info_t *o) {
+  cbvh::clear_error();
+  if (!h || !o) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  o->n_tris = h->n_tris;
+  o->n_nodes = h->n_nodes;
+  o->n_treelets = h->n_treelets;
+  o->blob_bytes = (int64_t)h->blob.size();
+  o->node_bytes = h->off_tris - h->off_treelets;
+  o->k = h->k;
+  o->branching = h->m;
+  o->quant_bits = h->bits;
+  o->treelet_bytes = h->treelet_bytes;
+  o->lattice_exp = h->e;
+  o->depth = h->depth;
+  o->max_treelet_depth = h->max_tdepth;
+  o->local_bits = h->lbits;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_blob_host(const cbvh_bvh *h, const uint8_t **blob, int64_t *bytes) {
+  cbvh::clear_error();
+  if (!h || !blob || !bytes) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  *blob = h->blob.data();
+  *bytes = (int64_t)h->blob.size();
+  return CBVH_OK;
+}
+
+namespace cbvh {
+namespace {
+thread_local std::string g_err;
+}
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+void clear_error() { g_err.clear(); }
+}  // namespace cbvh
+
+extern "C" const char *cbvh_last_error(void) { return cbvh::g_err.c_str(); }

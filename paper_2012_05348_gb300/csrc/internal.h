@@ -1,0 +1,30 @@
+// Private declarations shared by the host builder and the CUDA query code of libcbvh.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cbvh.h"
+
+struct cbvh_bvh {
+  // parameters
+  int k = 0, K = 0, m = 0, bits = 0, treelet_bytes = 0;
+  // derived layout
+  int e = 0;           // lattice step 2^e
+  int lbits = 1;       // node reference = (treelet << lbits) | local
+  int max_tdepth = 0;  // deepest node below its treelet root
+  int depth = 0;       // tree depth
+  int rec_bytes = 0, root_bytes = 0;
+  int64_t n_tris = 0, n_nodes = 0, n_treelets = 0;
+  int64_t off_treelets = 0, off_tris = 0;
+  std::vector<uint8_t> blob;  // host copy of the blob
+  // device copy (caller-owned memory)
+  void *dev_blob = nullptr;
+  int device = -1;
+};
+
+namespace cbvh {
+// Records a message for cbvh_last_error() and returns `code`.
+int fail(int code, const std::string &msg);
+void clear_error();
+}  // namespace cbvh

@@ -1,0 +1,1074 @@
+// CUDA kernels (sm_103a) and the device-side C ABI of libcbvh.
+//
+// Hot path: simultaneous traversal of two compressed k-DOP BVHs, Algorithm 1
+// (BVHtraversal) of Tan, Weller & Zachmann, for collision detection (CD) and proximity
+// query (PQ), one rigid pose of B per traversal, many poses per launch.
+//
+// Mapping: a persistent grid; each warp takes one pose at a time from a global counter and
+// runs the traversal with an explicit node-pair stack in shared memory.  Popping (a, b)
+// expands it the way Algorithm 1 recurses: the child sets of a and b (a node stands for
+// itself when it is a leaf) are decoded, every child pair is tested by one lane, and a
+// warp ballot compacts the survivors onto the stack; leaf pairs go to a queue that the
+// warp drains 32 at a time with one triangle-triangle test per lane (checkPrimitives).
+//
+// Decoding (abstract; Sec. III-B): a node's slab interval is its parent's decoded interval
+// corrected by b-bit deltas, so reaching a node means walking the chain of ancestors from
+// its treelet's absolute root.  Each warp keeps one decoded interval per depth below the
+// treelet root (tagged with the node reference); a chain walk stops at the deepest cached
+// ancestor, which in depth-first order is almost always the parent.
+//
+// Conservative tests: B's child is its decoded axis box, moved by the pose and projected on
+// each of A's directions d_j as [u_j.c + s_j - |u_j|.h, u_j.c + s_j + |u_j|.h] with
+// u_j = R^T d_j, s_j = d_j.t.  Every contributing operation rounds outward (directed-rounding
+// intrinsics) and the interval is widened by a bound on the rounding error of u_j, so a
+// pair is pruned only if its exact bounding volumes are disjoint.  PQ uses the same
+// intervals for the slab-gap lower bound max_j gap_j / |d_j|.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kMaxK = 13;   // directions of a 26-DOP
+constexpr int kMaxM = 16;   // branching factor
+constexpr unsigned kFull = 0xffffffffu;
+
+__constant__ int c_dir[kMaxK][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
+                                    {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                    {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
+
+// Device view of one BVH blob.
+struct BVd {
+  const uint8_t *blob;
+  const unsigned long long *toff;  // treelet byte offsets
+  const float4 *tris;              // 3 float4 per leaf slot
+  float scale;                     // 2^e
+  int K, bits, lbits, rec, root, tdepth;
+  uint32_t lmask;
+};
+
+// Per-warp shared-memory layout (byte offsets inside the warp's slice).
+struct Layout {
+  int warp_bytes;
+  int o_stack, stack_cap;
+  int o_leafq, leafq_cap;
+  int o_pose;
+  int o_tagA, o_latA, o_pathA;
+  int o_tagB, o_latB, o_pathB;
+  int o_aset, o_bset;
+  int KS;  // row stride (floats) of the per-child direction arrays
+};
+
+struct Params {
+  BVd A, B;
+  const float *poses;
+  int64_t n;
+  // CD
+  uint8_t *hit;
+  uint32_t *counts;         // per-pose pair counts (or null)
+  uint32_t *triples;        // (pose, i, j) scratch
+  unsigned long long cap;   // triple capacity
+  unsigned long long *pair_count;
+  uint32_t flags;
+  // PQ
+  float *dist;
+  // common
+  int32_t *status;
+  unsigned int *task_next;
+  unsigned long long *stats;  // [0] BV-pair tests, [1] leaf tests (checkPrimitives calls)
+  float invn[kMaxK];
+  Layout L;
+};
+
+__device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
+
+__device__ __forceinline__ const uint8_t *treelet_base(const BVd &X, uint32_t t) { return X.blob + X.toff[t]; }
+__device__ __forceinline__ const uint8_t *rec_at(const BVd &X, const uint8_t *tb, uint32_t l) {
+  return tb + 16 + (l ? X.root + (int)(l - 1) * X.rec : 0);
+}
+__device__ __forceinline__ uint32_t ld32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// Corrector of direction j in a non-root record.
+__device__ __forceinline__ int2 apply_delta(int2 P, const uint8_t *r, int bits, int j) {
+  uint32_t dl, dh;
+  if (bits == 8) {
+    uint32_t v = *reinterpret_cast<const uint16_t *>(r + 8 + 2 * j);
+    dl = v & 0xffu;
+    dh = v >> 8;
+  } else {
+    uint32_t v = ld32(r + 8 + 4 * j);
+    dl = v & 0xffffu;
+    dh = v >> 16;
+  }
+  uint32_t range = (uint32_t)P.y - (uint32_t)P.x;
+  int s = max(0, (32 - __clz((int)range)) - bits);
+  return make_int2((int)((uint32_t)P.x + (dl << s)), (int)((uint32_t)P.y - (dh << s)));
+}
+__device__ __forceinline__ int2 abs_lattice(const uint8_t *r, int j) {
+  return *reinterpret_cast<const int2 *>(r + 8 + 8 * j);
+}
+__device__ __forceinline__ float2 lat_to_f(int2 L, float scale) {
+  return make_float2(__fmul_rn(__int2float_rd(L.x), scale), __fmul_rn(__int2float_ru(L.y), scale));
+}
+__device__ __forceinline__ float2 abs_float(const uint8_t *r, int j) {
+  return *reinterpret_cast<const float2 *>(r + 8 + 8 * j);
+}
+
+// Warp-side decode cache of one BVH: per depth below a treelet root, the reference and the
+// decoded lattice interval (one column per direction) of the last node decoded there.
+struct Side {
+  uint32_t *tag;   // [tdepth + 1]
+  int2 *lat;       // [(tdepth + 1) * nd]
+  int *path;       // [tdepth + 1]
+  int nd;          // directions kept (K for A, 3 for B)
+  uint32_t cur_t;  // treelet whose base is cached
+  const uint8_t *cur_base;
+};
+
+// Decoded lattice interval of node x for direction j (lanes j < nd).  Walks up to the
+// deepest cached ancestor (or the treelet root), then applies the correctors down to x,
+// refreshing the cache on the way.  Returns x's record; all lanes must call it.
+__device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int lane, int2 &P) {
+  const uint32_t t = x >> X.lbits, l = x & X.lmask;
+  if (t != S.cur_t) {
+    S.cur_t = t;
+    S.cur_base = treelet_base(X, t);
+  }
+  const uint8_t *rx = rec_at(X, S.cur_base, l);
+  uint32_t w = ld32(rx);
+  const int d = (int)(w >> 24);
+  int dd = d, start = -1;
+  uint32_t ll = l;
+  const uint32_t tb = t << X.lbits;
+  for (;;) {
+    if (S.tag[dd] == (tb | ll)) {
+      start = dd;
+      break;
+    }
+    if (lane == 0) S.path[dd] = (int)ll;
+    if (dd == 0) break;
+    ll = w & 0xffffu;
+    w = ld32(rec_at(X, S.cur_base, ll));
+    --dd;
+  }
+  __syncwarp();
+  const bool act = lane < S.nd;
+  if (start < 0) {
+    if (act) {
+      P = abs_lattice(rec_at(X, S.cur_base, 0), lane);
+      S.lat[lane] = P;
+    }
+    if (lane == 0) S.tag[0] = tb;
+    start = 0;
+  } else if (act) {
+    P = S.lat[start * S.nd + lane];
+  }
+  for (int lev = start + 1; lev <= d; ++lev) {
+    const uint32_t pl = (uint32_t)S.path[lev];
+    if (act) {
+      P = apply_delta(P, rec_at(X, S.cur_base, pl), X.bits, lane);
+      S.lat[lev * S.nd + lane] = P;
+    }
+    if (lane == 0) S.tag[lev] = tb | pl;
+  }
+  __syncwarp();
+  return rx;
+}
+
+// Decode the set that Algorithm 1 expands for node x -- its children, or x itself when x is
+// a leaf or `force_self` -- into per-member FP32 slab bounds (dirs < nd) written to lo/hi
+// (row stride KS), references to ref[], and leaf slots (or 0xffffffff) to leaf[].  Returns
+// the number of members (warp-uniform).
+__device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float *lo, float *hi, int KS,
+                          uint32_t *ref, uint32_t *leaf) {
+  const uint32_t t = x >> X.lbits;
+  if (t != S.cur_t) {
+    S.cur_t = t;
+    S.cur_base = treelet_base(X, t);
+  }
+  const uint8_t *rx = rec_at(X, S.cur_base, x & X.lmask);
+  const uint32_t w0 = ld32(rx), w1 = ld32(rx + 4);
+  const int nc = (int)((w0 >> 16) & 31u);
+  const bool ext = (w0 >> 21) & 1u;
+  const bool self = force_self || nc == 0;
+  const int nd = S.nd;
+  if (X.bits == 0) {
+    if (self) {
+      if (lane < nd) {
+        float2 f = abs_float(rx, lane);
+        lo[lane] = f.x;
+        hi[lane] = f.y;
+      }
+      if (lane == 0) {
+        ref[0] = x;
+        leaf[0] = nc == 0 ? w1 : 0xffffffffu;
+      }
+    } else {
+      for (int it = lane; it < nc * nd; it += 32) {
+        const int i = it / nd, j = it - i * nd;
+        const uint8_t *rc;
+        uint32_t cref;
+        if (ext) {
+          cref = (w1 + i) << X.lbits;
+          rc = rec_at(X, treelet_base(X, w1 + i), 0);
+        } else {
+          cref = (t << X.lbits) | (w1 + i);
+          rc = rec_at(X, S.cur_base, w1 + i);
+        }
+        float2 f = abs_float(rc, j);
+        lo[i * KS + j] = f.x;
+        hi[i * KS + j] = f.y;
+        if (j == 0) {
+          const uint32_t cw0 = ld32(rc);
+          ref[i] = cref;
+          leaf[i] = ((cw0 >> 16) & 31u) == 0 ? ld32(rc + 4) : 0xffffffffu;
+        }
+      }
+    }
+    __syncwarp();
+    return self ? 1 : nc;
+  }
+  if (self || !ext) {
+    int2 P;
+    chain_decode(X, S, x, lane, P);
+    if (self) {
+      if (lane < nd) {
+        float2 f = lat_to_f(P, X.scale);
+        lo[lane] = f.x;
+        hi[lane] = f.y;
+      }
+      if (lane == 0) {
+        ref[0] = x;
+        leaf[0] = nc == 0 ? w1 : 0xffffffffu;
+      }
+      __syncwarp();
+      return 1;
+    }
+  }
+  const int d = (int)(w0 >> 24);
+  for (int it = lane; it < nc * nd; it += 32) {
+    const int i = it / nd, j = it - i * nd;
+    const uint8_t *rc;
+    uint32_t cref;
+    int2 L;
+    if (ext) {
+      cref = (w1 + i) << X.lbits;
+      rc = rec_at(X, treelet_base(X, w1 + i), 0);
+      L = abs_lattice(rc, j);
+    } else {
+      cref = (t << X.lbits) | (w1 + i);
+      rc = rec_at(X, S.cur_base, w1 + i);
+      L = apply_delta(S.lat[d * nd + j], rc, X.bits, j);
+    }
+    float2 f = lat_to_f(L, X.scale);
+    lo[i * KS + j] = f.x;
+    hi[i * KS + j] = f.y;
+    if (j == 0) {
+      const uint32_t cw0 = ld32(rc);
+      ref[i] = cref;
+      leaf[i] = ((cw0 >> 16) & 31u) == 0 ? ld32(rc + 4) : 0xffffffffu;
+    }
+  }
+  __syncwarp();
+  return nc;
+}
+
+// ---------------------------------------------------------------- triangle tests (FP32)
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 axpy(V3 a, float t, V3 d) { return {fmaf(t, d.x, a.x), fmaf(t, d.y, a.y), fmaf(t, d.z, a.z)}; }
+
+// Closed point-in-triangle test for a point on (or next to) the triangle's plane.
+__device__ __forceinline__ bool inside(const V3 *T, V3 N, V3 p) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    V3 e = sub(T[(k + 1) % 3], T[k]);
+    if (dot(N, cross(e, sub(p, T[k]))) < 0.f) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ float orient2(float ax, float ay, float bx, float by, float cx, float cy) {
+  return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+}
+__device__ __forceinline__ bool straddle(float a, float b) { return (a <= 0.f && b >= 0.f) || (a >= 0.f && b <= 0.f); }
+__device__ bool coplanar_hit(const V3 *P, const V3 *Q, V3 N) {
+  float ax = fabsf(N.x), ay = fabsf(N.y), az = fabsf(N.z);
+  int drop = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+  float p[3][2], q[3][2];
+  for (int i = 0; i < 3; ++i) {
+    const float a[3] = {P[i].x, P[i].y, P[i].z}, b[3] = {Q[i].x, Q[i].y, Q[i].z};
+    p[i][0] = a[drop == 0 ? 1 : 0];
+    p[i][1] = a[drop == 2 ? 1 : 2];
+    q[i][0] = b[drop == 0 ? 1 : 0];
+    q[i][1] = b[drop == 2 ? 1 : 2];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const float *a = p[i], *b = p[(i + 1) % 3], *c = q[j], *d = q[(j + 1) % 3];
+      float o1 = orient2(a[0], a[1], b[0], b[1], c[0], c[1]), o2 = orient2(a[0], a[1], b[0], b[1], d[0], d[1]);
+      float o3 = orient2(c[0], c[1], d[0], d[1], a[0], a[1]), o4 = orient2(c[0], c[1], d[0], d[1], b[0], b[1]);
+      if (o1 == 0.f && o2 == 0.f && o3 == 0.f && o4 == 0.f) {
+        bool sep = false;
+        for (int c2 = 0; c2 < 2; ++c2)
+          if (fmaxf(a[c2], b[c2]) < fminf(c[c2], d[c2]) || fmaxf(c[c2], d[c2]) < fminf(a[c2], b[c2])) sep = true;
+        if (!sep) return true;
+      } else if (straddle(o1, o2) && straddle(o3, o4)) {
+        return true;
+      }
+    }
+  auto in2 = [](const float (*t)[2], const float *x) {
+    float d1 = orient2(t[0][0], t[0][1], t[1][0], t[1][1], x[0], x[1]);
+    float d2 = orient2(t[1][0], t[1][1], t[2][0], t[2][1], x[0], x[1]);
+    float d3 = orient2(t[2][0], t[2][1], t[0][0], t[0][1], x[0], x[1]);
+    bool neg = d1 < 0.f || d2 < 0.f || d3 < 0.f, pos = d1 > 0.f || d2 > 0.f || d3 > 0.f;
+    return !(neg && pos);
+  };
+  return in2(q, p[0]) || in2(p, q[0]);
+}
+
+// Does some edge of Q (signed plane distances dq to P's plane) meet triangle P?
+__device__ __forceinline__ bool edges_meet(const V3 *P, V3 N, const V3 *Q, const float *dq) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3;
+    if (dq[i] == 0.f && inside(P, N, Q[i])) return true;
+    if ((dq[i] < 0.f && dq[j] > 0.f) || (dq[i] > 0.f && dq[j] < 0.f)) {
+      V3 x = axpy(Q[i], __fdividef(dq[i], dq[i] - dq[j]), sub(Q[j], Q[i]));
+      if (inside(P, N, x)) return true;
+    }
+  }
+  return false;
+}
+
+// Closed triangle-triangle intersection.  Triangles that are not coplanar meet iff an edge
+// of one meets the other (the ends of their common segment on the planes' intersection
+// line lie on edges); each edge is cut with the other triangle's plane and the cut point
+// tested against that triangle.  Coplanar triangles use a 2-D edge/containment test.
+// Inputs are in coordinates local to one vertex of P, so errors scale with the local size.
+__device__ bool tri_hit(const V3 *P, const V3 *Q) {
+  const V3 N1 = cross(sub(P[1], P[0]), sub(P[2], P[0]));
+  float dq[3], dp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dq[i] = dot(N1, sub(Q[i], P[0]));
+  if ((dq[0] > 0.f && dq[1] > 0.f && dq[2] > 0.f) || (dq[0] < 0.f && dq[1] < 0.f && dq[2] < 0.f)) return false;
+  const V3 N2 = cross(sub(Q[1], Q[0]), sub(Q[2], Q[0]));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dp[i] = dot(N2, sub(P[i], Q[0]));
+  if ((dp[0] > 0.f && dp[1] > 0.f && dp[2] > 0.f) || (dp[0] < 0.f && dp[1] < 0.f && dp[2] < 0.f)) return false;
+  if (dq[0] == 0.f && dq[1] == 0.f && dq[2] == 0.f) return coplanar_hit(P, Q, N1);
+  return edges_meet(P, N1, Q, dq) || edges_meet(Q, N2, P, dp);
+}
+
+__device__ __forceinline__ float pt_seg2(V3 p, V3 a, V3 b) {
+  V3 ab = sub(b, a), ap = sub(p, a);
+  float l2 = dot(ab, ab);
+  float t = l2 > 0.f ? __saturatef(__fdividef(dot(ap, ab), l2)) : 0.f;
+  V3 q = sub(axpy(a, t, ab), p);
+  return dot(q, q);
+}
+__device__ float pt_tri2(V3 p, const V3 *T) {
+  const V3 N = cross(sub(T[1], T[0]), sub(T[2], T[0]));
+  if (inside(T, N, p)) {
+    float s = dot(N, sub(p, T[0]));
+    return __fdividef(s * s, dot(N, N));
+  }
+  return fminf(pt_seg2(p, T[0], T[1]), fminf(pt_seg2(p, T[1], T[2]), pt_seg2(p, T[2], T[0])));
+}
+// Squared distance of segments [a, b] and [c, d]: the interior stationary point when it
+// lies in the unit square of parameters, else the best of the four endpoint-segment cases.
+__device__ float seg_seg2(V3 a, V3 b, V3 c, V3 d) {
+  V3 u = sub(b, a), v = sub(d, c), w = sub(a, c);
+  float A = dot(u, u), B = dot(u, v), C = dot(v, v), D = dot(u, w), E = dot(v, w);
+  float den = fmaf(A, C, -B * B);
+  float best = fminf(fminf(pt_seg2(a, c, d), pt_seg2(b, c, d)), fminf(pt_seg2(c, a, b), pt_seg2(d, a, b)));
+  if (den > 1e-20f * A * C) {
+    float s = __fdividef(fmaf(B, E, -C * D), den), t = __fdividef(fmaf(A, E, -B * D), den);
+    if (s >= 0.f && s <= 1.f && t >= 0.f && t <= 1.f) {
+      V3 q = sub(axpy(w, s, u), {t * v.x, t * v.y, t * v.z});
+      best = fminf(best, dot(q, q));
+    }
+  }
+  return best;
+}
+// Triangle-triangle distance: 0 when they meet, else the minimum over the 6 vertex-triangle
+// and 9 edge-edge cases.
+__device__ float tri_dist(const V3 *P, const V3 *Q) {
+  if (tri_hit(P, Q)) return 0.f;
+  float d2 = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d2 = fminf(d2, fminf(pt_tri2(P[i], Q), pt_tri2(Q[i], P)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d2 = fminf(d2, seg_seg2(P[i], P[(i + 1) % 3], Q[j], Q[(j + 1) % 3]));
+  return sqrtf(d2);
+}
+
+// Load leaf triangles: A's as stored, B's moved by the pose; both shifted so that A's first
+// vertex is the origin.  Returns the original triangle indices.
+__device__ __forceinline__ void load_pair(const Params &p, const float *pose, uint32_t sa, uint32_t sb, V3 *P, V3 *Q,
+                                          uint32_t &ia, uint32_t &ib) {
+  const float4 a0 = p.A.tris[3 * sa], a1 = p.A.tris[3 * sa + 1], a2 = p.A.tris[3 * sa + 2];
+  const float4 b0 = p.B.tris[3 * sb], b1 = p.B.tris[3 * sb + 1], b2 = p.B.tris[3 * sb + 2];
+  ia = __float_as_uint(a0.w);
+  ib = __float_as_uint(b0.w);
+  const V3 o = {a0.x, a0.y, a0.z};
+  P[0] = {0.f, 0.f, 0.f};
+  P[1] = sub({a1.x, a1.y, a1.z}, o);
+  P[2] = sub({a2.x, a2.y, a2.z}, o);
+  const float4 bb[3] = {b0, b1, b2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    V3 x;
+    x.x = fmaf(pose[0], bb[c].x, fmaf(pose[1], bb[c].y, fmaf(pose[2], bb[c].z, pose[9])));
+    x.y = fmaf(pose[3], bb[c].x, fmaf(pose[4], bb[c].y, fmaf(pose[5], bb[c].z, pose[10])));
+    x.z = fmaf(pose[6], bb[c].x, fmaf(pose[7], bb[c].y, fmaf(pose[8], bb[c].z, pose[11])));
+    Q[c] = sub(x, o);
+  }
+}
+
+enum { MODE_CD = 0, MODE_PQ = 1 };
+
+// Pose cache layout (floats): R[9], t[3], then per A-direction j: u[3], w[3], s_lo, s_hi, eta
+constexpr int kPoseJ = 9;
+__device__ __forceinline__ float *pose_dir(float *pc, int j) { return pc + 12 + kPoseJ * j; }
+
+template <int MODE>
+__global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  uint8_t *ws = smem + (threadIdx.x >> 5) * p.L.warp_bytes;
+  uint2 *stack = reinterpret_cast<uint2 *>(ws + p.L.o_stack);
+  uint2 *leafq = reinterpret_cast<uint2 *>(ws + p.L.o_leafq);
+  float *pc = reinterpret_cast<float *>(ws + p.L.o_pose);
+  const int KA = p.A.K, KS = p.L.KS;
+  Side SA{reinterpret_cast<uint32_t *>(ws + p.L.o_tagA), reinterpret_cast<int2 *>(ws + p.L.o_latA),
+          reinterpret_cast<int *>(ws + p.L.o_pathA), KA, 0xffffffffu, nullptr};
+  Side SB{reinterpret_cast<uint32_t *>(ws + p.L.o_tagB), reinterpret_cast<int2 *>(ws + p.L.o_latB),
+          reinterpret_cast<int *>(ws + p.L.o_pathB), 3, 0xffffffffu, nullptr};
+  float *alo = reinterpret_cast<float *>(ws + p.L.o_aset);
+  float *ahi = alo + kMaxM * KS;
+  uint32_t *aref = reinterpret_cast<uint32_t *>(ahi + kMaxM * KS);
+  uint32_t *aleaf = aref + kMaxM;
+  float *blo = reinterpret_cast<float *>(ws + p.L.o_bset);  // B child axis boxes [i][0..2]
+  float *bhi = blo + kMaxM * 4;
+  float *plo = bhi + kMaxM * 4;  // projected B boxes [i][KS]
+  float *phi = plo + kMaxM * KS;
+  uint32_t *bref = reinterpret_cast<uint32_t *>(phi + kMaxM * KS);
+  uint32_t *bleaf = bref + kMaxM;
+  for (int i = lane; i <= p.A.tdepth; i += 32) SA.tag[i] = 0xffffffffu;
+  for (int i = lane; i <= p.B.tdepth; i += 32) SB.tag[i] = 0xffffffffu;
+  __syncwarp();
+  const bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
+
+  for (;;) {
+    unsigned int task = 0;
+    if (lane == 0) task = atomicAdd(p.task_next, 1u);
+    task = __shfl_sync(kFull, task, 0);
+    if ((int64_t)task >= p.n) break;
+    const int64_t pose = task;
+    // ---- pose precompute: u_j = R^T d_j, |u_j|, [s_lo, s_hi] of d_j.t, and eta_j, a bound
+    // on the rounding error of each component of u_j ----
+    if (lane < 12) pc[lane] = p.poses[12 * pose + lane];
+    __syncwarp();
+    if (lane < KA) {
+      const int d0 = c_dir[lane][0], d1 = c_dir[lane][1], d2 = c_dir[lane][2];
+      float *q = pose_dir(pc, lane);
+      float smax = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float r0 = pc[c], r1 = pc[3 + c], r2 = pc[6 + c];
+        const float u = __fadd_rn(__fadd_rn(d0 * r0, d1 * r1), d2 * r2);
+        q[c] = u;
+        q[3 + c] = fabsf(u);
+        smax = fmaxf(smax, __fadd_ru(__fadd_ru(fabsf(d0 * r0), fabsf(d1 * r1)), fabsf(d2 * r2)));
+      }
+      q[6] = __fadd_rd(__fadd_rd(d0 * pc[9], d1 * pc[10]), d2 * pc[11]);
+      q[7] = __fadd_ru(__fadd_ru(d0 * pc[9], d1 * pc[10]), d2 * pc[11]);
+      q[8] = __fmul_ru(smax, 2.384185791015625e-07f);  // 2^-22
+    }
+    __syncwarp();
+
+    int sp = 0, nleaf = 0;
+    uint32_t nhits = 0;
+    float best = INFINITY;
+    bool done = false;
+    unsigned long long steps = 0, n_bv = 0, n_leaf = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    // checkPrimitives on the last `cnt` queued leaf pairs, one pair per lane
+    auto drain = [&](int cnt) {
+      nleaf -= cnt;
+      n_leaf += cnt;
+      bool h = false;
+      float dl = INFINITY;
+      uint32_t ia = 0, ib = 0;
+      if (lane < cnt) {
+        const uint2 e = leafq[nleaf + lane];
+        V3 P[3], Q[3];
+        load_pair(p, pc, e.x, e.y, P, Q, ia, ib);
+        if (MODE == MODE_CD)
+          h = tri_hit(P, Q);
+        else
+          dl = tri_dist(P, Q);
+      }
+      __syncwarp();
+      if (MODE == MODE_CD) {
+        const unsigned mh = __ballot_sync(kFull, h);
+        if (mh) {
+          nhits += __popc(mh);
+          if (p.counts) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(p.pair_count, (unsigned long long)__popc(mh));
+            b0 = __shfl_sync(kFull, b0, 0);
+            if (h) {
+              const unsigned long long slot = b0 + __popc(mh & lt);
+              if (slot < p.cap) {
+                p.triples[3 * slot] = (uint32_t)pose;
+                p.triples[3 * slot + 1] = ia;
+                p.triples[3 * slot + 2] = ib;
+              }
+            }
+          }
+          if (early) done = true;
+        }
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dl = fminf(dl, __shfl_xor_sync(kFull, dl, o));
+        best = fminf(best, dl);
+        if (best == 0.f) done = true;
+      }
+    };
+    // the root pair is tested before recursing: expand it as a pair of singleton sets
+    uint32_t a = 0, b = 0;
+    bool root = true;
+    while (!done) {
+      // ---------------- expand (a, b) as Algorithm 1 does ----------------
+      const int na = decode_set(p.A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
+      const int nb = decode_set(p.B, SB, b, root, lane, blo, bhi, 4, bref, bleaf);
+      root = false;
+      // project B's member boxes onto A's directions
+      for (int it = lane; it < nb * KA; it += 32) {
+        const int i = it / KA, j = it - i * KA;
+        const float *q = pose_dir(pc, j);
+        float c[3], h[3], M = 0.f;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const float lo = blo[i * 4 + x], hi = bhi[i * 4 + x];
+          c[x] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+          h[x] = fmaxf(__fsub_ru(hi, c[x]), __fsub_ru(c[x], lo));
+          M = __fadd_ru(M, __fadd_ru(fabsf(c[x]), h[x]));
+        }
+        const float mlo = __fmaf_rd(q[0], c[0], __fmaf_rd(q[1], c[1], __fmaf_rd(q[2], c[2], q[6])));
+        const float mhi = __fmaf_ru(q[0], c[0], __fmaf_ru(q[1], c[1], __fmaf_ru(q[2], c[2], q[7])));
+        const float rad = __fmaf_ru(q[3], h[0], __fmaf_ru(q[4], h[1], __fmul_ru(q[5], h[2])));
+        const float sl = __fmul_ru(q[8], M);
+        plo[i * KS + j] = __fsub_rd(__fsub_rd(mlo, rad), sl);
+        phi[i * KS + j] = __fadd_ru(__fadd_ru(mhi, rad), sl);
+      }
+      __syncwarp();
+      // test every member pair; survivors are compacted by ballot onto the stack (inner
+      // pairs) or the leaf queue (leaf pairs)
+      const int np = na * nb;
+      n_bv += np;
+      float run_lb = INFINITY;  // PQ: smallest lower bound pushed by this expansion ...
+      int run_pos = -1;         // ... and its stack slot
+      for (int base = 0; base < np && !done; base += 32) {
+        const int it = base + lane;
+        bool keep = false;
+        int i = 0, j = 0;
+        float lb = INFINITY;
+        if (it < np) {
+          i = it / nb;
+          j = it - i * nb;
+          const float *al = alo + i * KS, *ah = ahi + i * KS, *pl = plo + j * KS, *ph = phi + j * KS;
+          if (MODE == MODE_CD) {
+            keep = true;
+            for (int d = 0; d < KA; ++d) keep &= (al[d] <= ph[d]) & (pl[d] <= ah[d]);
+          } else {
+            lb = 0.f;
+            for (int d = 0; d < KA; ++d) {
+              const float g = fmaxf(__fsub_rd(al[d], ph[d]), __fsub_rd(pl[d], ah[d]));
+              lb = fmaxf(lb, __fmul_rd(g, p.invn[d]));
+            }
+            keep = lb < best;
+          }
+        }
+        const bool isleaf = keep && aleaf[i] != 0xffffffffu && bleaf[j] != 0xffffffffu;
+        const unsigned ml = __ballot_sync(kFull, isleaf);
+        const unsigned mi = __ballot_sync(kFull, keep && !isleaf);
+        if (sp + __popc(mi) > p.L.stack_cap) {
+          if (lane == 0) set_status(p.status, CBVH_ERR_STACK);
+          done = true;
+          break;
+        }
+        const int pos = sp + __popc(mi & lt);
+        if (isleaf) leafq[nleaf + __popc(ml & lt)] = make_uint2(aleaf[i], bleaf[j]);
+        if (keep && !isleaf) stack[pos] = make_uint2(aref[i], bref[j]);
+        if (MODE == MODE_PQ && mi) {
+          float ml_ = (keep && !isleaf) ? lb : INFINITY;
+          int mp = pos;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(kFull, ml_, o);
+            const int op = __shfl_xor_sync(kFull, mp, o);
+            if (ov < ml_ || (ov == ml_ && op < mp)) {
+              ml_ = ov;
+              mp = op;
+            }
+          }
+          if (ml_ < run_lb) {
+            run_lb = ml_;
+            run_pos = mp;
+          }
+        }
+        nleaf += __popc(ml);
+        sp += __popc(mi);
+        __syncwarp();
+        while (nleaf >= 32 && !done) drain(32);
+      }
+      // PQ: the most promising child pair goes on top, so it is expanded next
+      if (MODE == MODE_PQ && run_pos >= 0 && run_pos != sp - 1 && !done) {
+        if (lane == 0) {
+          const uint2 x = stack[run_pos];
+          stack[run_pos] = stack[sp - 1];
+          stack[sp - 1] = x;
+        }
+        __syncwarp();
+      }
+      if (++steps > (1ull << 40)) {
+        if (lane == 0) set_status(p.status, CBVH_ERR_TIMEOUT);
+        done = true;
+      }
+      if (done || sp == 0) break;
+      // ---------------- pop ----------------
+      const uint2 e = stack[--sp];
+      a = e.x;
+      b = e.y;
+      __syncwarp();
+    }
+    while (!done && nleaf > 0) drain(min(nleaf, 32));
+    if (lane == 0) {
+      atomicAdd(&p.stats[0], n_bv);
+      atomicAdd(&p.stats[1], n_leaf);
+      if (MODE == MODE_CD) {
+        p.hit[pose] = nhits ? 1 : 0;
+        if (p.counts) p.counts[pose] = nhits;
+      } else {
+        p.dist[pose] = best;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- output compaction
+// Exclusive scan of per-pose counts into int64 offsets (one CTA, tiles of 1024 x 4);
+// offsets[n] = total, also stored in *needed; flags capacity overflow in *status.
+__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t *counts, int64_t n, int64_t *offsets,
+                                                    int64_t *needed, unsigned long long cap, int32_t *status) {
+  __shared__ long long warp_sums[32];
+  __shared__ long long carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += 4096) {
+    long long v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = base + 4 * tid + k;
+      v[k] = i < n ? counts[i] : 0;
+      s += v[k];
+    }
+    long long incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      long long ws = warp_sums[lane], wi = ws;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += y;
+      }
+      warp_sums[lane] = wi - ws;
+    }
+    __syncthreads();
+    long long run = carry_s + warp_sums[wid] + incl - s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = base + 4 * tid + k;
+      if (i < n) offsets[i] = run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (tid == 1023) carry_s = run;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    offsets[n] = carry_s;
+    if (needed) *needed = carry_s;
+    if ((unsigned long long)carry_s > cap) set_status(status, CBVH_ERR_CAPACITY);
+  }
+}
+
+// Scatter (pose, i, j) triples into each pose's CSR segment (order within a pose arbitrary).
+__global__ void scatter_kernel(const uint32_t *triples, const unsigned long long *count, unsigned long long cap,
+                               const int64_t *offsets, uint32_t *cursor, int32_t *pairs) {
+  const unsigned long long total = *count;
+  if (total > cap) return;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t pose = triples[3 * t];
+    const uint32_t slot = atomicSub(&cursor[pose], 1u) - 1u;
+    const int64_t o = offsets[pose] + slot;
+    pairs[2 * o] = (int32_t)triples[3 * t + 1];
+    pairs[2 * o + 1] = (int32_t)triples[3 * t + 2];
+  }
+}
+
+// Sort each pose's pairs by (i, j): bitonic network whose first stage of every merge
+// compares mirrored elements, so that padding beyond the segment acts as +infinity.
+constexpr int kSortSmem = 4096;
+__device__ __forceinline__ void cmp_swap(unsigned long long *k, int i, int j) {
+  unsigned long long a = k[i], b = k[j];
+  if (a > b) {
+    k[i] = b;
+    k[j] = a;
+  }
+}
+__device__ void bitonic(unsigned long long *k, int n) {
+  int N = 1;
+  while (N < n) N <<= 1;
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int j = i ^ (size - 1);
+      if (j > i && j < n) cmp_swap(k, i, j);
+    }
+    __syncthreads();
+    for (int s = size >> 2; s > 0; s >>= 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int j = i ^ s;
+        if (j > i && j < n) cmp_swap(k, i, j);
+      }
+      __syncthreads();
+    }
+  }
+}
+__global__ void __launch_bounds__(256) sort_kernel(const int64_t *offsets, int64_t n, const unsigned long long *count,
+                                                   unsigned long long cap, int32_t *pairs) {
+  __shared__ unsigned long long keys[kSortSmem];
+  if (*count > cap) return;
+  for (int64_t pose = blockIdx.x; pose < n; pose += gridDim.x) {
+    const int64_t o = offsets[pose];
+    const int cnt = (int)(offsets[pose + 1] - o);
+    if (cnt < 2) continue;
+    unsigned long long *seg = reinterpret_cast<unsigned long long *>(pairs + 2 * o);
+    unsigned long long *k = cnt <= kSortSmem ? keys : seg;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const uint32_t ai = (uint32_t)pairs[2 * (o + i)], bi = (uint32_t)pairs[2 * (o + i) + 1];
+      k[i] = ((unsigned long long)ai << 32) | bi;
+    }
+    __syncthreads();
+    bitonic(k, cnt);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const unsigned long long v = k[i];
+      pairs[2 * (o + i)] = (int32_t)(v >> 32);
+      pairs[2 * (o + i) + 1] = (int32_t)(v & 0xffffffffu);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- decode test hook
+// One block per treelet; thread items (local node, direction) walk their node's chain from
+// the treelet root.  Output in blob order.
+__global__ void decode_all_kernel(const BVd X, int32_t *lat_out, float *f_out) {
+  const uint32_t t = blockIdx.x;
+  const uint8_t *tb = treelet_base(X, t);
+  const uint32_t cnt = ld32(tb), first = ld32(tb + 4);
+  for (uint32_t it = threadIdx.x; it < cnt * (uint32_t)X.K; it += blockDim.x) {
+    const uint32_t l = it / X.K, j = it - l * X.K;
+    const uint8_t *r = rec_at(X, tb, l);
+    float2 f;
+    if (X.bits == 0) {
+      f = abs_float(r, j);
+    } else {
+      uint32_t path[64];
+      int d = 0;
+      for (uint32_t y = l; y != 0 && d < 64; y = ld32(rec_at(X, tb, y)) & 0xffffu) path[d++] = y;
+      int2 P = abs_lattice(rec_at(X, tb, 0), j);
+      for (int q = d - 1; q >= 0; --q) P = apply_delta(P, rec_at(X, tb, path[q]), X.bits, j);
+      f = lat_to_f(P, X.scale);
+      if (lat_out) {
+        lat_out[((size_t)(first + l) * X.K + j) * 2] = P.x;
+        lat_out[((size_t)(first + l) * X.K + j) * 2 + 1] = P.y;
+      }
+    }
+    if (f_out) {
+      f_out[((size_t)(first + l) * X.K + j) * 2] = f.x;
+      f_out[((size_t)(first + l) * X.K + j) * 2 + 1] = f.y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+BVd view(const cbvh_bvh *h) {
+  BVd v;
+  const uint8_t *b = static_cast<const uint8_t *>(h->dev_blob);
+  v.blob = b;
+  v.toff = reinterpret_cast<const unsigned long long *>(b + 64);
+  v.tris = reinterpret_cast<const float4 *>(b + h->off_tris);
+  v.scale = std::ldexp(1.0f, h->e);
+  v.K = h->K;
+  v.bits = h->bits;
+  v.lbits = h->lbits;
+  v.rec = h->rec_bytes;
+  v.root = h->root_bytes;
+  v.tdepth = h->max_tdepth;
+  v.lmask = (h->lbits >= 32) ? 0xffffffffu : ((1u << h->lbits) - 1u);
+  return v;
+}
+
+int align16(int x) { return (x + 15) & ~15; }
+
+Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
+  Layout L;
+  const int KA = A->K;
+  L.KS = (KA & 1) ? KA : KA + 1;
+  // stack bound: every level of the node-pair tree leaves at most (mA mB - 1) siblings
+  L.stack_cap = 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1);
+  L.leafq_cap = 64;  // < 32 queued before a round, a round adds <= 32
+  int o = 0;
+  L.o_stack = o;
+  o = align16(o + 8 * L.stack_cap);
+  L.o_leafq = o;
+  o = align16(o + 8 * L.leafq_cap);
+  L.o_pose = o;
+  o = align16(o + 4 * (12 + kPoseJ * KA));
+  L.o_tagA = o;
+  o = align16(o + 4 * (A->max_tdepth + 1));
+  L.o_latA = o;
+  o = align16(o + 8 * (A->max_tdepth + 1) * KA);
+  L.o_pathA = o;
+  o = align16(o + 4 * (A->max_tdepth + 1));
+  L.o_tagB = o;
+  o = align16(o + 4 * (B->max_tdepth + 1));
+  L.o_latB = o;
+  o = align16(o + 8 * (B->max_tdepth + 1) * 3);
+  L.o_pathB = o;
+  o = align16(o + 4 * (B->max_tdepth + 1));
+  L.o_aset = o;
+  o = align16(o + 4 * (2 * kMaxM * L.KS + 2 * kMaxM));
+  L.o_bset = o;
+  o = align16(o + 4 * (2 * kMaxM * 4 + 2 * kMaxM * L.KS + 2 * kMaxM));
+  L.warp_bytes = o;
+  return L;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return cbvh::fail(CBVH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kWarpsPerBlock = 4;
+
+// Optional profiling events recorded around the traversal launch (per host thread).
+thread_local cudaEvent_t g_prof_before = nullptr, g_prof_after = nullptr;
+
+struct Launch {
+  int blocks, smem;
+};
+
+template <int MODE>
+int launch_traverse(const Params &p, cudaStream_t s) {
+  const int smem = kWarpsPerBlock * p.L.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(traverse_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_kernel<MODE>, 32 * kWarpsPerBlock, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
+  int64_t need = (p.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int blocks = (int)std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(need, 1));
+  if (g_prof_before) cudaEventRecord(g_prof_before, s);
+  traverse_kernel<MODE><<<blocks, 32 * kWarpsPerBlock, smem, s>>>(p);
+  e = cudaGetLastError();
+  if (g_prof_after) cudaEventRecord(g_prof_after, s);
+  if (e != cudaSuccess) return cuda_fail(e, "traverse launch");
+  return CBVH_OK;
+}
+
+// workspace: [0, 256) counters, then per-pose counts (u32), then (pose, i, j) triples
+constexpr int64_t kWsHeader = 256;
+int64_t ws_bytes(int64_t n, int mode, int64_t cap) {
+  int64_t b = kWsHeader;
+  if (mode == 0) b += (4 * n + 15) / 16 * 16 + 12 * std::max<int64_t>(cap, 0);
+  return b;
+}
+
+int check_pair(const cbvh_bvh *A, const cbvh_bvh *B) {
+  if (!A || !B) return cbvh::fail(CBVH_ERR_ARG, "NULL handle");
+  if (!A->dev_blob || !B->dev_blob) return cbvh::fail(CBVH_ERR_STATE, "handle has no device blob; call cbvh_attach");
+  return CBVH_OK;
+}
+
+void fill_params(Params &p, const cbvh_bvh *A, const cbvh_bvh *B) {
+  std::memset(&p, 0, sizeof p);
+  p.A = view(A);
+  p.B = view(B);
+  p.L = make_layout(A, B);
+  for (int j = 0; j < kMaxK; ++j) {
+    static const int n2[kMaxK] = {1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3};
+    float f = (float)(1.0 / std::sqrt((double)n2[j]));
+    while ((double)f * (double)f * n2[j] > 1.0) f = std::nextafter(f, 0.0f);
+    p.invn[j] = f;
+  }
+}
+
+}  // namespace
+
+extern "C" int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *stream) {
+  cbvh::clear_error();
+  if (!h || !dev_blob) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  if (bytes < (int64_t)h->blob.size()) return cbvh::fail(CBVH_ERR_ARG, "device buffer smaller than the blob");
+  if (reinterpret_cast<uintptr_t>(dev_blob) & 255) return cbvh::fail(CBVH_ERR_ARG, "device buffer not 256-byte aligned");
+  cudaError_t e = cudaMemcpyAsync(dev_blob, h->blob.data(), h->blob.size(), cudaMemcpyHostToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  h->dev_blob = dev_blob;
+  cudaGetDevice(&h->device);
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_decode_all(const cbvh_bvh *h, int32_t *lattice_out, float *bounds_out, void *stream) {
+  cbvh::clear_error();
+  if (!h) return cbvh::fail(CBVH_ERR_ARG, "NULL handle");
+  if (!h->dev_blob) return cbvh::fail(CBVH_ERR_STATE, "handle has no device blob; call cbvh_attach");
+  decode_all_kernel<<<(unsigned)h->n_treelets, 128, 0, static_cast<cudaStream_t>(stream)>>>(view(h), lattice_out,
+                                                                                             bounds_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "decode launch");
+}
+
+extern "C" int cbvh_workspace_bytes(const cbvh_bvh *A, const cbvh_bvh *B, int64_t n, int mode, int64_t cap,
+                                    int64_t *bytes) {
+  cbvh::clear_error();
+  if (!A || !B || !bytes || n < 0 || (mode != 0 && mode != 1)) return cbvh::fail(CBVH_ERR_ARG, "bad argument");
+  *bytes = ws_bytes(n, mode, cap);
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, uint8_t *hit,
+                            int64_t *pair_offsets, int32_t *pairs, int64_t pair_capacity, int64_t *pairs_needed,
+                            uint32_t flags, void *workspace, int64_t workspace_bytes, int32_t *status,
+                            void *stream) {
+  cbvh::clear_error();
+  if (int rc = check_pair(A, B)) return rc;
+  if (n < 0 || (n > 0 && (!poses || !hit)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
+  if (n > 0xffffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
+  const bool want_pairs = pair_offsets != nullptr || pairs != nullptr;
+  if (want_pairs && (!pair_offsets || !pairs || pair_capacity < 0))
+    return cbvh::fail(CBVH_ERR_ARG, "pair_offsets and pairs must be given together");
+  if (want_pairs && (flags & CBVH_EARLY_EXIT)) return cbvh::fail(CBVH_ERR_ARG, "CBVH_EARLY_EXIT returns no pairs");
+  const int64_t need = ws_bytes(n, 0, want_pairs ? pair_capacity : 0);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or misaligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  cudaError_t e = cudaMemsetAsync(ws, 0, want_pairs ? kWsHeader + 4 * n : kWsHeader, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (n == 0) {
+    if (want_pairs) {
+      e = cudaMemsetAsync(pair_offsets, 0, sizeof(int64_t), s);
+      if (e == cudaSuccess && pairs_needed) e = cudaMemsetAsync(pairs_needed, 0, sizeof(int64_t), s);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    return CBVH_OK;
+  }
+  Params p;
+  fill_params(p, A, B);
+  p.poses = poses;
+  p.n = n;
+  p.hit = hit;
+  p.flags = flags;
+  p.status = status;
+  p.task_next = reinterpret_cast<unsigned int *>(ws);
+  p.pair_count = reinterpret_cast<unsigned long long *>(ws + 8);
+  p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+  uint32_t *counts = reinterpret_cast<uint32_t *>(ws + kWsHeader);
+  uint32_t *triples = reinterpret_cast<uint32_t *>(ws + kWsHeader + (4 * n + 15) / 16 * 16);
+  if (want_pairs) {
+    p.counts = counts;
+    p.triples = triples;
+    p.cap = (unsigned long long)pair_capacity;
+  }
+  if (int rc = launch_traverse<MODE_CD>(p, s)) return rc;
+  if (want_pairs) {
+    scan_kernel<<<1, 1024, 0, s>>>(counts, n, pair_offsets, pairs_needed, p.cap, status);
+    scatter_kernel<<<1024, 256, 0, s>>>(triples, p.pair_count, p.cap, pair_offsets, counts, pairs);
+    if (flags & CBVH_SORT_PAIRS) sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(pair_offsets, n, p.pair_count, p.cap, pairs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "compaction launch");
+  }
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist,
+                             void *workspace, int64_t workspace_bytes, int32_t *status, void *stream) {
+  cbvh::clear_error();
+  if (int rc = check_pair(A, B)) return rc;
+  if (n < 0 || (n > 0 && (!poses || !dist)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
+  if (n > 0xffffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
+  if (!workspace || workspace_bytes < ws_bytes(n, 1, 0) || (reinterpret_cast<uintptr_t>(workspace) & 15))
+    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or misaligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(workspace, 0, kWsHeader, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (n == 0) return CBVH_OK;
+  Params p;
+  fill_params(p, A, B);
+  p.poses = poses;
+  p.n = n;
+  p.dist = dist;
+  p.status = status;
+  p.task_next = static_cast<unsigned int *>(workspace);
+  p.stats = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(workspace) + 16);
+  return launch_traverse<MODE_PQ>(p, s);
+}
+
+extern "C" int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream) {
+  cbvh::clear_error();
+  if (!workspace || !stats_host) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(stats_host, static_cast<const uint8_t *>(workspace) + 16, 2 * sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "cbvh_query_stats");
+}
+
+extern "C" int cbvh_profile_events(void *before, void *after) {
+  cbvh::clear_error();
+  if ((before == nullptr) != (after == nullptr)) return cbvh::fail(CBVH_ERR_ARG, "give both events or neither");
+  g_prof_before = static_cast<cudaEvent_t>(before);
+  g_prof_after = static_cast<cudaEvent_t>(after);
+  return CBVH_OK;
+}

@@ -1,0 +1,102 @@
+"""The C-ABI library on the CPU: it builds, loads and exports every entry point the header
+declares, its host builder/encoder reproduces the oracle's blob byte for byte, and host-side
+argument errors come back as error codes (no GPU compute is run here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def cb():
+    from paper_2012_05348_gb300 import _build
+    _build.build()
+    import paper_2012_05348_gb300 as m
+    return m
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "cbvh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cbvh_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(cb):
+    syms = declared_symbols()
+    assert len(syms) >= 10
+    lib = C.CDLL(cb.LIB_PATH)
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+CONFIGS = [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096), (26, 16, 16, 8192), (18, 4, 0, 4096),
+           (24, 8, 16, 65536), (18, 2, 16, 131072), (18, 16, 8, 32768)]
+
+
+@pytest.mark.parametrize("k,m,bits,tb", CONFIGS)
+def test_blob_identical_to_oracle(cb, k, m, bits, tb):
+    v, t = synth.icosphere(3, 1.0, 0.15, seed=k + m + bits)
+    o = oracle.BVH(v, t, k, m, bits, tb)
+    h = cb.BVH(v, t, k, m, bits, tb, device=None)
+    assert h.info["n_nodes"] == o.n_nodes and h.info["n_treelets"] == o.n_treelets
+    assert h.info["lattice_exp"] == o.e and h.info["depth"] == o.depth
+    bo, bl = o.blob(), h.blob_host()
+    assert len(bo) == len(bl) and (bo == bl).all()
+
+
+def test_blob_identical_to_oracle_terrain_and_odd_meshes(cb):
+    va, ta, _ = synth.heightfield(96, seed=31)
+    for v, t in [(va, ta), synth.box_mesh((1.0, 2.0, 3.0)), synth.capsule(0.5, 0.1, 2000, seed=3),
+                 (np.array([[0, 0, 0], [1e-3, 0, 0], [0, 2e-3, 1e-4]], np.float32), np.array([[0, 1, 2]], np.int32)),
+                 (np.array([[1e6, 1e6, 1e6], [1e6 + 64, 1e6, 1e6], [1e6, 1e6 + 64, 1e6 - 32]], np.float32),
+                  np.array([[0, 1, 2]], np.int32))]:
+        for k, m, bits, tb in [(24, 8, 8, 16384), (18, 4, 16, 4096)]:
+            o = oracle.BVH(v, t, k, m, bits, tb)
+            h = cb.BVH(v, t, k, m, bits, tb, device=None)
+            assert (o.blob() == h.blob_host()).all()
+
+
+def test_build_errors(cb):
+    v, t = synth.icosphere(1, seed=1)
+    for args, code in [((5, 4, 8, 4096), -1), ((18, 3, 8, 4096), -1), ((18, 4, 12, 4096), -1),
+                       ((18, 4, 8, 5000), -1), ((18, 4, 8, 2048), -1)]:
+        with pytest.raises(cb.CbvhError) as e:
+            cb.BVH(v, t, *args, device=None)
+        assert e.value.code == code
+    bad = t.copy()
+    bad[3, 1] = -1
+    with pytest.raises(cb.CbvhError) as e:
+        cb.BVH(v, bad, device=None)
+    assert e.value.code == -2
+    deg = t.copy()
+    deg[0] = (2, 2, 5)
+    with pytest.raises(cb.CbvhError) as e:
+        cb.BVH(v, deg, device=None)
+    assert e.value.code == -2
+    nan = v.copy()
+    nan[0, 0] = np.nan
+    with pytest.raises(cb.CbvhError) as e:
+        cb.BVH(nan, t, device=None)
+    assert e.value.code == -2
+
+
+def test_queries_without_device_blob_are_rejected(cb):
+    v, t = synth.icosphere(1, seed=1)
+    A = cb.BVH(v, t, device=None)
+    B = cb.BVH(v, t, device=None)
+    st = C.c_int32()
+    rc = cb.lib.cbvh_collide(A.handle, B.handle, None, 0, None, None, None, 0, None, 0, None, 0, C.byref(st), None)
+    assert rc == -9
+    rc = cb.lib.cbvh_distance(A.handle, B.handle, None, 0, None, None, 0, C.byref(st), None)
+    assert rc == -9
+    out = C.c_int64()
+    assert cb.lib.cbvh_workspace_bytes(A.handle, B.handle, 100, 0, 1000, C.byref(out)) == 0
+    assert out.value >= 256 + 400 + 12000
+    assert cb.lib.cbvh_workspace_bytes(A.handle, B.handle, -1, 0, 0, C.byref(out)) == -1
