@@ -68,6 +68,8 @@ def lib():
         L.or_distance.argtypes = [P, P, P, I64, I32, P, P]
         L.or_brute_distance.argtypes = [P, P, P, I64, P]
         L.or_near_contact.argtypes = [P, P, P, I64, D, P, P]
+        L.or_near_pairs.argtypes = [P, P, P, I64, D, P]
+        L.or_near_pairs.restype = C.c_void_p
         L.or_pairs_total.argtypes = [P]
         L.or_pairs_total.restype = I64
         L.or_pairs_copy.argtypes = [P, P, P]
@@ -221,6 +223,14 @@ def near_contact(A: BVH, B: BVH, poses, eps: float):
     margin = np.zeros(len(P))
     lib().or_near_contact(A.handle, B.handle, _p(P), len(P), float(eps), _p(near), _p(margin))
     return near.astype(bool), margin
+
+
+def near_pairs(A: BVH, B: BVH, poses, eps: float):
+    """Per pose, the triangle pairs within eps of a contact decision: (offsets, pairs)."""
+    P = _poses(poses)
+    cnt = np.zeros(len(P), np.int64)
+    h = lib().or_near_pairs(A.handle, B.handle, _p(P), len(P), float(eps), _p(cnt))
+    return _take_pairs(h, len(P))
 
 
 def _tri(T):

@@ -1152,13 +1152,18 @@ static void check_primitives(tctx *c, int mode, int32_t a, int32_t b) {
     if (d < c->best) c->best = d;
   } else {
     double m;
+    int amb = 0;
     if (or_tri_intersect(T1, T2, &m)) {
       if (m < c->min_margin) c->min_margin = m;
-      if (m < c->eps) c->near = 1;
+      amb = m < c->eps;
     } else {
       double d = or_tri_dist(T1, T2);
       if (d < c->min_margin) c->min_margin = d;
-      if (d <= c->eps) c->near = 1;
+      amb = d <= c->eps;
+    }
+    if (amb) {
+      c->near = 1;
+      if (c->pairs) pv_push(c->pairs, ta, tb);
     }
   }
 }
@@ -1317,6 +1322,25 @@ void or_near_contact(const or_bvh *A, const or_bvh *B, const float *poses, int64
     near[p] = (uint8_t)c.near;
     if (margin) margin[p] = c.min_margin;
   }
+}
+
+/* The near-contact pairs themselves: per pose, the sorted (i, j) pairs that are separated
+ * by at most eps or intersect with a decision margin below eps -- the pairs for which an
+ * FP32 test may legitimately decide either way. */
+or_pairs *or_near_pairs(const or_bvh *A, const or_bvh *B, const float *poses, int64_t n, double eps, int64_t *counts) {
+  or_pairs *P = (or_pairs *)calloc(1, sizeof(or_pairs));
+  P->n = n;
+  P->v = (pvec *)calloc((size_t)n, sizeof(pvec));
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t p = 0; p < n; ++p) {
+    tctx c;
+    ctx_init(&c, A, B, poses + 12 * p, 0, eps);
+    c.pairs = &P->v[p];
+    if (bv_overlap(&c, 0, 0)) bvh_traversal(&c, MODE_NEAR, 0, 0);
+    counts[p] = c.pairs->n;
+    if (c.pairs->n > 1) qsort(c.pairs->ij, (size_t)c.pairs->n, 2 * sizeof(int32_t), cmp_pair);
+  }
+  return P;
 }
 
 /* Brute force over all triangle pairs (the plain definitions of CD and PQ).  A pair whose

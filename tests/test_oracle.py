@@ -385,6 +385,7 @@ def test_near_contact_filter_against_brute_force(c1_small):
     D = synth.scene_diameter(va, vb)
     eps = 1e-3 * D  # a wide band so that several poses are flagged
     near, margin = oracle.near_contact(A, B, c["poses"][:10], eps)
+    n_off, n_ij = oracle.near_pairs(A, B, c["poses"][:10], eps)
     for p in range(10):
         pose = c["poses"][p]
         R, t = pose[:9].reshape(3, 3).astype(np.float64), pose[9:].astype(np.float64)
@@ -394,6 +395,7 @@ def test_near_contact_filter_against_brute_force(c1_small):
         lo_b, hi_b = TB.min(1), TB.max(1)
         flagged = False
         mmin = math.inf
+        amb = []
         for i in range(len(TA)):
             ok = ((lo_a[i] - eps <= hi_b) & (lo_b <= hi_a[i] + eps)).all(1)
             for j in np.nonzero(ok)[0]:
@@ -402,6 +404,8 @@ def test_near_contact_filter_against_brute_force(c1_small):
                 mmin = min(mmin, q)
                 if (hit and m < eps) or (not hit and q <= eps):
                     flagged = True
+                    amb.append((i, int(j)))
         assert flagged == bool(near[p])
+        assert sorted(amb) == [tuple(x) for x in n_ij[n_off[p]:n_off[p + 1]].tolist()]
         if math.isfinite(mmin) and mmin <= eps:
             assert margin[p] == pytest.approx(mmin, rel=1e-12)
