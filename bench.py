@@ -235,32 +235,25 @@ def main():
     # ---- timed: device-resident inputs; L2 flushed (untimed) before every step ----
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    kcd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    kpq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", "") or "")
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    cb.profile_collect()
+    cb.profile_enable(True)
     with ClockSampler(uuid or None) as clk:
         for s in range(K):
             flush.zero_()
             ev[s][0].record(stream)
-            cb.profile_events(*kcd[s])
-            rc = L.cbvh_collide(A.handle, B.handle, P(poses), n, P(hit), P(off), P(pairs), cap, P(need),
-                                cb.SORT_PAIRS, P(ws_cd), ws_cd_b, P(st_cd), sp)
-            cb.profile_events(*kpq[s])
-            rc |= L.cbvh_distance(A.handle, B.handle, P(poses), n, P(dist_out), P(ws_pq), ws_pq_b, P(st_pq), sp)
-            cb.profile_events(None, None)
+            step(poses)
             ev[s][1].record(stream)
-            if rc:
-                raise cb.CbvhError(rc, L.cbvh_last_error().decode())
         torch.cuda.synchronize()
+    cb.profile_enable(False)
+    prof = cb.profile_collect()
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    cd_ms = [a.elapsed_time(b) for a, b in kcd]
-    pq_ms = [a.elapsed_time(b) for a, b in kpq]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -305,7 +298,8 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     cd_bytes = bv_cd * BYTES_BV + leaf_cd * BYTES_LEAF + n * BYTES_POSE + n_pairs * 3 * 4
     pq_bytes = bv_pq * BYTES_BV + leaf_pq * BYTES_LEAF + n * BYTES_POSE
-    cd_avg, pq_avg = statistics.mean(cd_ms), statistics.mean(pq_ms)
+    cd_avg = prof["collide"][0] / max(1, prof["collide"][1])
+    pq_avg = prof["distance"][0] / max(1, prof["distance"][1])
     dom = ("traverse_kernel<CD>", cd_bytes, cd_avg) if cd_avg >= pq_avg else ("traverse_kernel<PQ>", pq_bytes, pq_avg)
     achieved = dom[1] / (dom[2] / 1e3) / 1e9
     traffic = None
@@ -330,8 +324,8 @@ def main():
                    "poses": n, "step": "CD with sorted pair lists + PQ, every pose",
                    "l2": "flushed (256 MB write, untimed) before every timed step",
                    "parallelism": f"replicas x{world}"},
-        "cd_pose_queries_per_s": n / (statistics.mean(cd_ms) / 1e3),
-        "pq_pose_queries_per_s": n / (statistics.mean(pq_ms) / 1e3),
+        "cd_pose_queries_per_s": n / (cd_avg / 1e3),
+        "pq_pose_queries_per_s": n / (pq_avg / 1e3),
         "bv_pair_tests_per_s": (bv_cd + bv_pq) * K / (total_ms / 1e3),
         "bv_pair_tests_per_step": bv_cd + bv_pq, "leaf_tests_per_step": leaf_cd + leaf_pq,
         "pairs_per_step": n_pairs,

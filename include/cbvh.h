@@ -100,7 +100,7 @@ int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *stream);
  * bounds (lo rounded down, hi rounded up).  Asynchronous on `stream`. */
 int cbvh_decode_all(const cbvh_bvh *h, int32_t *lattice_out, float *bounds_out, void *stream);
 
-/* Bytes of device workspace a query needs (16-byte aligned pointer, contents need not be
+/* Bytes of device workspace a query needs (256-byte aligned pointer, contents need not be
  * initialised).  mode: 0 = collide, 1 = distance; pair_capacity is ignored for distance
  * and for collide without pair outputs. */
 int cbvh_workspace_bytes(const cbvh_bvh *A, const cbvh_bvh *B, int64_t n_poses, int mode, int64_t pair_capacity,
@@ -131,11 +131,15 @@ int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int6
  * synchronises `stream`.  The paper has no such call; it feeds the BV-pair tests/s metric. */
 int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream);
 
-/* Profiling: when both are non-NULL, every later query on this host thread records the
- * CUDA event `before` immediately before its traversal kernel and `after` immediately after
- * it, on the query's stream, so that the traversal kernel can be timed alone.  NULL, NULL
- * turns it off.  Events are cudaEvent_t handles created by the caller. */
-int cbvh_profile_events(void *before, void *after);
+/* Profiling of the traversal kernel alone.  While enabled (on != 0), every query on this
+ * host thread records a pair of library-owned CUDA events on its stream immediately around
+ * its traversal kernel.  The paper has no such call; it feeds the roofline measurement. */
+int cbvh_profile_enable(int on);
+
+/* Waits for the recorded event pairs of this host thread and returns, per mode (index 0 =
+ * collide, 1 = distance), the summed traversal-kernel time in ms (ms_host[2]) and the
+ * number of launches (launches_host[2]); then forgets them. */
+int cbvh_profile_collect(double *ms_host, int64_t *launches_host);
 
 #ifdef __cplusplus
 }

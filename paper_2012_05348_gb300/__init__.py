@@ -18,7 +18,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["BVH", "collide", "distance", "workspace_bytes", "query_stats", "profile_events", "CbvhError", "lib",
+__all__ = ["BVH", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect", "CbvhError", "lib",
            "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
 LIB_PATH = _build.LIB
@@ -49,9 +49,11 @@ def _declare(L):
     L.cbvh_collide.argtypes = [P, P, P, I64, P, P, P, I64, P, U32, P, I64, P, P]
     L.cbvh_distance.argtypes = [P, P, P, I64, P, P, I64, P, P]
     L.cbvh_query_stats.argtypes = [P, P, P]
-    L.cbvh_profile_events.argtypes = [P, P]
+    L.cbvh_profile_enable.argtypes = [I32]
+    L.cbvh_profile_collect.argtypes = [P, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
-              "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_events"):
+              "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
+              "cbvh_profile_collect"):
         getattr(L, f).restype = I32
     return L
 
@@ -209,11 +211,17 @@ def query_stats(workspace, stream=None):
     return int(out[0]), int(out[1])
 
 
-def profile_events(before=None, after=None):
-    """Record torch.cuda.Event `before` / `after` around every later traversal launch."""
-    b = C.c_void_p(before.cuda_event) if before is not None else C.c_void_p(0)
-    a = C.c_void_p(after.cuda_event) if after is not None else C.c_void_p(0)
-    _check(_load().cbvh_profile_events(b, a))
+def profile_enable(on: bool = True):
+    """Time every later traversal kernel launch of this thread with library-owned events."""
+    _check(_load().cbvh_profile_enable(int(bool(on))))
+
+
+def profile_collect():
+    """{'collide': (ms, launches), 'distance': (ms, launches)} since the last collect."""
+    ms = np.zeros(2)
+    n = np.zeros(2, np.int64)
+    _check(_load().cbvh_profile_collect(ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
+    return {"collide": (float(ms[0]), int(n[0])), "distance": (float(ms[1]), int(n[1]))}
 
 
 def distance(A: BVH, B: BVH, poses, *, stream=None, check: bool = True):

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -36,6 +37,8 @@ namespace {
 constexpr int kMaxK = 13;   // directions of a 26-DOP
 constexpr int kMaxM = 16;   // branching factor
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kThreads = 32 * kWarpsPerBlock;
 
 __constant__ int c_dir[kMaxK][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
                                     {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
@@ -78,8 +81,17 @@ struct Params {
   float *dist;
   // common
   int32_t *status;
-  unsigned int *task_next;
   unsigned long long *stats;  // [0] BV-pair tests, [1] leaf tests (checkPrimitives calls)
+  // rounds
+  int round, last_round, budget;
+  uint32_t spill_below;       // a round hands work on only while it has fewer tasks than this
+  uint32_t task_cap;
+  unsigned int *task_next;    // this round's task cursor
+  const unsigned int *count_in;
+  unsigned int *count_out;
+  const uint4 *tasks_in;      // (pose, a, b, 0)
+  uint4 *tasks_out;
+  uint2 *stacks;              // per-warp node-pair stacks, L.stack_cap entries each
   float invn[kMaxK];
   Layout L;
 };
@@ -439,16 +451,56 @@ __device__ __forceinline__ void load_pair(const Params &p, const float *pose, ui
 
 enum { MODE_CD = 0, MODE_PQ = 1 };
 
-// Pose cache layout (floats): R[9], t[3], then per A-direction j: u[3], w[3], s_lo, s_hi, eta
+// Pose cache layout (floats): R[9], t[3], then per A-direction j: u[3], |u|[3], s_lo, s_hi, eta
 constexpr int kPoseJ = 9;
 __device__ __forceinline__ float *pose_dir(float *pc, int j) { return pc + 12 + kPoseJ * j; }
 
+// Conservative interval of d_j . (R x + t) over B-member i: the exact posed triangle when the
+// member is a leaf, otherwise its decoded axis box.  q = pose_dir(pc, j).
+__device__ __forceinline__ float2 project_member(const Params &p, const float *q, const float *blo,
+                                                 const float *bhi, uint32_t leaf, int i) {
+  if (leaf != 0xffffffffu) {
+    const float4 *T = p.B.tris + 3 * (size_t)leaf;
+    float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const float4 x = T[v];
+      const float l = __fmaf_rd(q[0], x.x, __fmaf_rd(q[1], x.y, __fmaf_rd(q[2], x.z, q[6])));
+      const float h = __fmaf_ru(q[0], x.x, __fmaf_ru(q[1], x.y, __fmaf_ru(q[2], x.z, q[7])));
+      const float sl = __fmul_ru(q[8], __fadd_ru(__fadd_ru(fabsf(x.x), fabsf(x.y)), fabsf(x.z)));
+      lo = fminf(lo, __fsub_rd(l, sl));
+      hi = fmaxf(hi, __fadd_ru(h, sl));
+    }
+    return make_float2(lo, hi);
+  }
+  float c[3], h[3], M = 0.f;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const float lo = blo[i * 4 + x], hi = bhi[i * 4 + x];
+    c[x] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
+    h[x] = fmaxf(__fsub_ru(hi, c[x]), __fsub_ru(c[x], lo));
+    M = __fadd_ru(M, __fadd_ru(fabsf(c[x]), h[x]));
+  }
+  const float mlo = __fmaf_rd(q[0], c[0], __fmaf_rd(q[1], c[1], __fmaf_rd(q[2], c[2], q[6])));
+  const float mhi = __fmaf_ru(q[0], c[0], __fmaf_ru(q[1], c[1], __fmaf_ru(q[2], c[2], q[7])));
+  const float rad = __fmaf_ru(q[3], h[0], __fmaf_ru(q[4], h[1], __fmul_ru(q[5], h[2])));
+  const float sl = __fmul_ru(q[8], M);
+  return make_float2(__fsub_rd(__fsub_rd(mlo, rad), sl), __fadd_ru(__fadd_ru(mhi, rad), sl));
+}
+
+// One round of the traversal.  Tasks are node pairs of one pose still to be expanded: in
+// round 0 the root pair of every pose, afterwards the pairs that earlier rounds handed on.
+// A warp runs Algorithm 1 depth-first from its task with an explicit stack; in a round that
+// may hand work on, a task that has used its expansion budget moves its whole stack into
+// the next round's task buffer, so that the node-pair tree of a heavy pose is spread over
+// many warps.  The last round has no budget and finishes every task.
 template <int MODE>
-__global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
+__global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31;
-  uint8_t *ws = smem + (threadIdx.x >> 5) * p.L.warp_bytes;
-  uint2 *stack = reinterpret_cast<uint2 *>(ws + p.L.o_stack);
+  const int wib = threadIdx.x >> 5;
+  uint8_t *ws = smem + wib * p.L.warp_bytes;
+  uint2 *stack = p.stacks + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * (size_t)p.L.stack_cap;
   uint2 *leafq = reinterpret_cast<uint2 *>(ws + p.L.o_leafq);
   float *pc = reinterpret_cast<float *>(ws + p.L.o_pose);
   const int KA = p.A.K, KS = p.L.KS;
@@ -460,9 +512,9 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
   float *ahi = alo + kMaxM * KS;
   uint32_t *aref = reinterpret_cast<uint32_t *>(ahi + kMaxM * KS);
   uint32_t *aleaf = aref + kMaxM;
-  float *blo = reinterpret_cast<float *>(ws + p.L.o_bset);  // B child axis boxes [i][0..2]
+  float *blo = reinterpret_cast<float *>(ws + p.L.o_bset);  // B member axis boxes [i][0..2]
   float *bhi = blo + kMaxM * 4;
-  float *plo = bhi + kMaxM * 4;  // projected B boxes [i][KS]
+  float *plo = bhi + kMaxM * 4;  // B members projected on A's directions [i][KS]
   float *phi = plo + kMaxM * KS;
   uint32_t *bref = reinterpret_cast<uint32_t *>(phi + kMaxM * KS);
   uint32_t *bleaf = bref + kMaxM;
@@ -470,41 +522,80 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
   for (int i = lane; i <= p.B.tdepth; i += 32) SB.tag[i] = 0xffffffffu;
   __syncwarp();
   const bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n_in = p.round == 0 ? (uint32_t)p.n : min(*p.count_in, p.task_cap);
+  const bool may_spill = !p.last_round && n_in < p.spill_below;
+  unsigned long long n_bv = 0, n_leaf = 0;
+  int64_t cur_pose = -1;
 
   for (;;) {
     unsigned int task = 0;
     if (lane == 0) task = atomicAdd(p.task_next, 1u);
     task = __shfl_sync(kFull, task, 0);
-    if ((int64_t)task >= p.n) break;
-    const int64_t pose = task;
-    // ---- pose precompute: u_j = R^T d_j, |u_j|, [s_lo, s_hi] of d_j.t, and eta_j, a bound
-    // on the rounding error of each component of u_j ----
-    if (lane < 12) pc[lane] = p.poses[12 * pose + lane];
-    __syncwarp();
-    if (lane < KA) {
-      const int d0 = c_dir[lane][0], d1 = c_dir[lane][1], d2 = c_dir[lane][2];
-      float *q = pose_dir(pc, lane);
-      float smax = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float r0 = pc[c], r1 = pc[3 + c], r2 = pc[6 + c];
-        const float u = __fadd_rn(__fadd_rn(d0 * r0, d1 * r1), d2 * r2);
-        q[c] = u;
-        q[3 + c] = fabsf(u);
-        smax = fmaxf(smax, __fadd_ru(__fadd_ru(fabsf(d0 * r0), fabsf(d1 * r1)), fabsf(d2 * r2)));
-      }
-      q[6] = __fadd_rd(__fadd_rd(d0 * pc[9], d1 * pc[10]), d2 * pc[11]);
-      q[7] = __fadd_ru(__fadd_ru(d0 * pc[9], d1 * pc[10]), d2 * pc[11]);
-      q[8] = __fmul_ru(smax, 2.384185791015625e-07f);  // 2^-22
+    if (task >= n_in) break;
+    uint32_t pose, a, b;
+    bool root;
+    if (p.round == 0) {
+      pose = task;
+      a = b = 0;
+      root = true;
+    } else {
+      const uint4 t = p.tasks_in[task];
+      pose = t.x;
+      a = t.y;
+      b = t.z;
+      root = false;
     }
-    __syncwarp();
+    if ((int64_t)pose != cur_pose) {
+      // ---- pose precompute: u_j = R^T d_j, |u_j|, [s_lo, s_hi] of d_j.t, and eta_j, a
+      // bound on the rounding error of each component of u_j ----
+      cur_pose = pose;
+      if (lane < 12) pc[lane] = p.poses[12 * (size_t)pose + lane];
+      __syncwarp();
+      if (lane < KA) {
+        const int d0 = c_dir[lane][0], d1 = c_dir[lane][1], d2 = c_dir[lane][2];
+        float *q = pose_dir(pc, lane);
+        float smax = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float r0 = pc[c], r1 = pc[3 + c], r2 = pc[6 + c];
+          const float u = __fadd_rn(__fadd_rn(d0 * r0, d1 * r1), d2 * r2);
+          q[c] = u;
+          q[3 + c] = fabsf(u);
+          smax = fmaxf(smax, __fadd_ru(__fadd_ru(fabsf(d0 * r0), fabsf(d1 * r1)), fabsf(d2 * r2)));
+        }
+        q[6] = __fadd_rd(__fadd_rd(d0 * pc[9], d1 * pc[10]), d2 * pc[11]);
+        q[7] = __fadd_ru(__fadd_ru(d0 * pc[9], d1 * pc[10]), d2 * pc[11]);
+        q[8] = __fmul_ru(smax, 2.384185791015625e-07f);  // 2^-22
+      }
+      __syncwarp();
+    }
+    // per-pose state: the root task initialises it; later tasks update it atomically
+    float best = INFINITY;
+    if (root) {
+      if (lane == 0) {
+        if (MODE == MODE_CD) {
+          p.hit[pose] = 0;
+          if (p.counts) p.counts[pose] = 0;
+        } else {
+          p.dist[pose] = INFINITY;
+        }
+      }
+    } else if (MODE == MODE_PQ) {
+      float v = 0.f;
+      if (lane == 0) v = *reinterpret_cast<volatile float *>(&p.dist[pose]);
+      best = __shfl_sync(kFull, v, 0);
+    } else if (early) {
+      int h = 0;
+      if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&p.hit[pose]);
+      if (__shfl_sync(kFull, h, 0)) continue;
+    }
+    float published = best;
 
     int sp = 0, nleaf = 0;
     uint32_t nhits = 0;
-    float best = INFINITY;
     bool done = false;
-    unsigned long long steps = 0, n_bv = 0, n_leaf = 0;
-    const unsigned lt = (1u << lane) - 1u;
+    int expansions = 0;
     // checkPrimitives on the last `cnt` queued leaf pairs, one pair per lane
     auto drain = [&](int cnt) {
       nleaf -= cnt;
@@ -533,7 +624,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
             if (h) {
               const unsigned long long slot = b0 + __popc(mh & lt);
               if (slot < p.cap) {
-                p.triples[3 * slot] = (uint32_t)pose;
+                p.triples[3 * slot] = pose;
                 p.triples[3 * slot + 1] = ia;
                 p.triples[3 * slot + 2] = ib;
               }
@@ -545,35 +636,25 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dl = fminf(dl, __shfl_xor_sync(kFull, dl, o));
         best = fminf(best, dl);
+        if (best < published) {
+          if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&p.dist[pose]), __float_as_uint(best));
+          published = best;
+        }
         if (best == 0.f) done = true;
       }
     };
-    // the root pair is tested before recursing: expand it as a pair of singleton sets
-    uint32_t a = 0, b = 0;
-    bool root = true;
-    while (!done) {
+
+    for (;;) {
       // ---------------- expand (a, b) as Algorithm 1 does ----------------
       const int na = decode_set(p.A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
       const int nb = decode_set(p.B, SB, b, root, lane, blo, bhi, 4, bref, bleaf);
       root = false;
-      // project B's member boxes onto A's directions
+      ++expansions;
       for (int it = lane; it < nb * KA; it += 32) {
         const int i = it / KA, j = it - i * KA;
-        const float *q = pose_dir(pc, j);
-        float c[3], h[3], M = 0.f;
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          const float lo = blo[i * 4 + x], hi = bhi[i * 4 + x];
-          c[x] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
-          h[x] = fmaxf(__fsub_ru(hi, c[x]), __fsub_ru(c[x], lo));
-          M = __fadd_ru(M, __fadd_ru(fabsf(c[x]), h[x]));
-        }
-        const float mlo = __fmaf_rd(q[0], c[0], __fmaf_rd(q[1], c[1], __fmaf_rd(q[2], c[2], q[6])));
-        const float mhi = __fmaf_ru(q[0], c[0], __fmaf_ru(q[1], c[1], __fmaf_ru(q[2], c[2], q[7])));
-        const float rad = __fmaf_ru(q[3], h[0], __fmaf_ru(q[4], h[1], __fmul_ru(q[5], h[2])));
-        const float sl = __fmul_ru(q[8], M);
-        plo[i * KS + j] = __fsub_rd(__fsub_rd(mlo, rad), sl);
-        phi[i * KS + j] = __fadd_ru(__fadd_ru(mhi, rad), sl);
+        const float2 r = project_member(p, pose_dir(pc, j), blo, bhi, bleaf[i], i);
+        plo[i * KS + j] = r.x;
+        phi[i * KS + j] = r.y;
       }
       __syncwarp();
       // test every member pair; survivors are compacted by ballot onto the stack (inner
@@ -615,19 +696,19 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
         if (isleaf) leafq[nleaf + __popc(ml & lt)] = make_uint2(aleaf[i], bleaf[j]);
         if (keep && !isleaf) stack[pos] = make_uint2(aref[i], bref[j]);
         if (MODE == MODE_PQ && mi) {
-          float ml_ = (keep && !isleaf) ? lb : INFINITY;
+          float mv = (keep && !isleaf) ? lb : INFINITY;
           int mp = pos;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(kFull, ml_, o);
+            const float ov = __shfl_xor_sync(kFull, mv, o);
             const int op = __shfl_xor_sync(kFull, mp, o);
-            if (ov < ml_ || (ov == ml_ && op < mp)) {
-              ml_ = ov;
+            if (ov < mv || (ov == mv && op < mp)) {
+              mv = ov;
               mp = op;
             }
           }
-          if (ml_ < run_lb) {
-            run_lb = ml_;
+          if (mv < run_lb) {
+            run_lb = mv;
             run_pos = mp;
           }
         }
@@ -636,7 +717,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
         __syncwarp();
         while (nleaf >= 32 && !done) drain(32);
       }
-      // PQ: the most promising child pair goes on top, so it is expanded next
+      // PQ: the most promising child pair goes on top, so that it is expanded next
       if (MODE == MODE_PQ && run_pos >= 0 && run_pos != sp - 1 && !done) {
         if (lane == 0) {
           const uint2 x = stack[run_pos];
@@ -645,11 +726,47 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
         }
         __syncwarp();
       }
-      if (++steps > (1ull << 40)) {
-        if (lane == 0) set_status(p.status, CBVH_ERR_TIMEOUT);
-        done = true;
-      }
       if (done || sp == 0) break;
+      // ---------------- hand the rest of this task on ----------------
+      if (may_spill && expansions >= p.budget && sp >= 2) {
+        uint32_t base = 0;
+        int ok = 0;
+        if (lane == 0) {
+          uint32_t old = *reinterpret_cast<volatile uint32_t *>(p.count_out);
+          for (int tries = 0; tries < 64; ++tries) {
+            if ((unsigned long long)old + sp > p.task_cap) break;
+            const uint32_t prev = atomicCAS(p.count_out, old, old + (uint32_t)sp);
+            if (prev == old) {
+              ok = 1;
+              base = old;
+              break;
+            }
+            old = prev;
+          }
+        }
+        ok = __shfl_sync(kFull, ok, 0);
+        base = __shfl_sync(kFull, base, 0);
+        if (ok) {
+          for (int k = lane; k < sp; k += 32) {
+            const uint2 e = stack[k];
+            p.tasks_out[base + k] = make_uint4(pose, e.x, e.y, 0u);
+          }
+          sp = 0;
+          __syncwarp();
+          break;
+        }
+      }
+      if ((expansions & 15) == 0) {
+        if (MODE == MODE_PQ) {
+          float v = 0.f;
+          if (lane == 0) v = *reinterpret_cast<volatile float *>(&p.dist[pose]);
+          best = fminf(best, __shfl_sync(kFull, v, 0));
+        } else if (early) {
+          int h = 0;
+          if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&p.hit[pose]);
+          if (__shfl_sync(kFull, h, 0)) break;
+        }
+      }
       // ---------------- pop ----------------
       const uint2 e = stack[--sp];
       a = e.x;
@@ -657,17 +774,22 @@ __global__ void __launch_bounds__(128) traverse_kernel(const Params p) {
       __syncwarp();
     }
     while (!done && nleaf > 0) drain(min(nleaf, 32));
+    nleaf = 0;
     if (lane == 0) {
-      atomicAdd(&p.stats[0], n_bv);
-      atomicAdd(&p.stats[1], n_leaf);
       if (MODE == MODE_CD) {
-        p.hit[pose] = nhits ? 1 : 0;
-        if (p.counts) p.counts[pose] = nhits;
-      } else {
-        p.dist[pose] = best;
+        if (nhits) {
+          p.hit[pose] = 1;
+          if (p.counts) atomicAdd(&p.counts[pose], nhits);
+        }
+      } else if (best < published) {
+        atomicMin(reinterpret_cast<unsigned int *>(&p.dist[pose]), __float_as_uint(best));
       }
     }
     __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&p.stats[0], n_bv);
+    atomicAdd(&p.stats[1], n_leaf);
   }
 }
 
@@ -851,10 +973,9 @@ Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
   L.KS = (KA & 1) ? KA : KA + 1;
   // stack bound: every level of the node-pair tree leaves at most (mA mB - 1) siblings
   L.stack_cap = 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1);
-  L.leafq_cap = 64;  // < 32 queued before a round, a round adds <= 32
+  L.leafq_cap = 64;  // < 32 queued before a round of tests, a round adds <= 32
   int o = 0;
-  L.o_stack = o;
-  o = align16(o + 8 * L.stack_cap);
+  L.o_stack = -1;  // stacks live in global memory
   L.o_leafq = o;
   o = align16(o + 8 * L.leafq_cap);
   L.o_pose = o;
@@ -883,42 +1004,106 @@ int cuda_fail(cudaError_t e, const char *what) {
   return cbvh::fail(CBVH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr int kWarpsPerBlock = 4;
-
-// Optional profiling events recorded around the traversal launch (per host thread).
-thread_local cudaEvent_t g_prof_before = nullptr, g_prof_after = nullptr;
-
-struct Launch {
-  int blocks, smem;
+// Optional per-thread profiling of the traversal launches: an event pair is recorded around
+// each launch on its stream and summed by cbvh_profile_collect.
+struct ProfRec {
+  cudaEvent_t a, b;
+  int mode;
 };
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> used, spare;
+};
+thread_local Profiler g_prof;
+
+// Rounds of a query and the expansion budget of a task in each (0 = none, last round).
+constexpr int kRounds = 6;
+constexpr int kBudget[kRounds] = {16, 32, 64, 128, 256, 0};
+constexpr int kMaxWarpsPerSM = 64;
+
+// Workspace layout: [0, 256) counters -- u64 pair count at 0, u64 stats[2] at 16, u32 task
+// cursor per round at 64, u32 task count per round at 128 -- then the per-pose pair counts
+// and (pose, i, j) triples (collide with pairs), two task buffers and the per-warp stacks.
+constexpr int64_t kWsHeader = 256;
+struct WsPlan {
+  int64_t counts, triples, tasks0, tasks1, stacks, total;
+  uint32_t task_cap;
+  int warps_max;
+};
+int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
+WsPlan ws_plan(const Layout &L, int64_t n, int mode, int64_t cap, int sms) {
+  WsPlan w;
+  int64_t o = kWsHeader;
+  w.counts = o;
+  if (mode == 0) o = align256(o + 4 * n);
+  w.triples = o;
+  if (mode == 0) o = align256(o + 12 * std::max<int64_t>(cap, 0));
+  const int64_t tcap = std::min<int64_t>(std::max<int64_t>(int64_t(1) << 20, 256 * n), int64_t(1) << 30);
+  w.task_cap = (uint32_t)tcap;
+  w.tasks0 = o;
+  o = align256(o + 16 * tcap);
+  w.tasks1 = o;
+  o = align256(o + 16 * tcap);
+  w.warps_max = sms * kMaxWarpsPerSM;
+  w.stacks = o;
+  o = align256(o + (int64_t)w.warps_max * L.stack_cap * 8);
+  w.total = o;
+  return w;
+}
+
+int device_sms(int *sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "device query");
+}
 
 template <int MODE>
-int launch_traverse(const Params &p, cudaStream_t s) {
+int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t s) {
   const int smem = kWarpsPerBlock * p.L.warp_bytes;
   cudaError_t e = cudaFuncSetAttribute(traverse_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_kernel<MODE>, 32 * kWarpsPerBlock, smem);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_kernel<MODE>, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
-  int64_t need = (p.n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  int blocks = (int)std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(need, 1));
-  if (g_prof_before) cudaEventRecord(g_prof_before, s);
-  traverse_kernel<MODE><<<blocks, 32 * kWarpsPerBlock, smem, s>>>(p);
+  per_sm = std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock);
+  const int blocks = sms * per_sm;
+  unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64);
+  unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128);
+  uint4 *buf[2] = {reinterpret_cast<uint4 *>(ws + w.tasks0), reinterpret_cast<uint4 *>(ws + w.tasks1)};
+  p.stacks = reinterpret_cast<uint2 *>(ws + w.stacks);
+  p.task_cap = w.task_cap;
+  p.spill_below = (uint32_t)std::min<int64_t>((int64_t)blocks * kWarpsPerBlock * 16, w.task_cap);
+  ProfRec rec{nullptr, nullptr, MODE};
+  if (g_prof.on) {
+    if (!g_prof.spare.empty()) {
+      rec = g_prof.spare.back();
+      g_prof.spare.pop_back();
+      rec.mode = MODE;
+    } else if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess) {
+      return cbvh::fail(CBVH_ERR_CUDA, "cudaEventCreate");
+    }
+    cudaEventRecord(rec.a, s);
+  }
+  for (int r = 0; r < kRounds; ++r) {
+    p.round = r;
+    p.last_round = r == kRounds - 1;
+    p.budget = kBudget[r];
+    p.task_next = next + r;
+    p.count_in = count + r;
+    p.count_out = count + r + 1;
+    p.tasks_in = buf[(r + 1) & 1];
+    p.tasks_out = buf[r & 1];
+    traverse_kernel<MODE><<<blocks, kThreads, smem, s>>>(p);
+  }
   e = cudaGetLastError();
-  if (g_prof_after) cudaEventRecord(g_prof_after, s);
+  if (g_prof.on) {
+    cudaEventRecord(rec.b, s);
+    g_prof.used.push_back(rec);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "traverse launch");
   return CBVH_OK;
-}
-
-// workspace: [0, 256) counters, then per-pose counts (u32), then (pose, i, j) triples
-constexpr int64_t kWsHeader = 256;
-int64_t ws_bytes(int64_t n, int mode, int64_t cap) {
-  int64_t b = kWsHeader;
-  if (mode == 0) b += (4 * n + 15) / 16 * 16 + 12 * std::max<int64_t>(cap, 0);
-  return b;
 }
 
 int check_pair(const cbvh_bvh *A, const cbvh_bvh *B) {
@@ -971,7 +1156,9 @@ extern "C" int cbvh_workspace_bytes(const cbvh_bvh *A, const cbvh_bvh *B, int64_
                                     int64_t *bytes) {
   cbvh::clear_error();
   if (!A || !B || !bytes || n < 0 || (mode != 0 && mode != 1)) return cbvh::fail(CBVH_ERR_ARG, "bad argument");
-  *bytes = ws_bytes(n, mode, cap);
+  int sms = 0;
+  if (int rc = device_sms(&sms)) return rc;
+  *bytes = ws_plan(make_layout(A, B), n, mode, cap, sms).total;
   return CBVH_OK;
 }
 
@@ -982,17 +1169,21 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
   cbvh::clear_error();
   if (int rc = check_pair(A, B)) return rc;
   if (n < 0 || (n > 0 && (!poses || !hit)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
-  if (n > 0xffffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
+  if (n > 0x7fffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
   const bool want_pairs = pair_offsets != nullptr || pairs != nullptr;
   if (want_pairs && (!pair_offsets || !pairs || pair_capacity < 0))
     return cbvh::fail(CBVH_ERR_ARG, "pair_offsets and pairs must be given together");
   if (want_pairs && (flags & CBVH_EARLY_EXIT)) return cbvh::fail(CBVH_ERR_ARG, "CBVH_EARLY_EXIT returns no pairs");
-  const int64_t need = ws_bytes(n, 0, want_pairs ? pair_capacity : 0);
-  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 15))
-    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or misaligned");
+  int sms = 0;
+  if (int rc = device_sms(&sms)) return rc;
+  Params p;
+  fill_params(p, A, B);
+  const WsPlan w = ws_plan(p.L, n, 0, want_pairs ? pair_capacity : 0, sms);
+  if (!workspace || workspace_bytes < w.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint8_t *ws = static_cast<uint8_t *>(workspace);
-  cudaError_t e = cudaMemsetAsync(ws, 0, want_pairs ? kWsHeader + 4 * n : kWsHeader, s);
+  cudaError_t e = cudaMemsetAsync(ws, 0, kWsHeader, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   if (n == 0) {
@@ -1003,28 +1194,26 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
     }
     return CBVH_OK;
   }
-  Params p;
-  fill_params(p, A, B);
   p.poses = poses;
   p.n = n;
   p.hit = hit;
   p.flags = flags;
   p.status = status;
-  p.task_next = reinterpret_cast<unsigned int *>(ws);
-  p.pair_count = reinterpret_cast<unsigned long long *>(ws + 8);
+  p.pair_count = reinterpret_cast<unsigned long long *>(ws);
   p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
-  uint32_t *counts = reinterpret_cast<uint32_t *>(ws + kWsHeader);
-  uint32_t *triples = reinterpret_cast<uint32_t *>(ws + kWsHeader + (4 * n + 15) / 16 * 16);
+  uint32_t *counts = reinterpret_cast<uint32_t *>(ws + w.counts);
+  uint32_t *triples = reinterpret_cast<uint32_t *>(ws + w.triples);
   if (want_pairs) {
     p.counts = counts;
     p.triples = triples;
     p.cap = (unsigned long long)pair_capacity;
   }
-  if (int rc = launch_traverse<MODE_CD>(p, s)) return rc;
+  if (int rc = launch_rounds<MODE_CD>(p, ws, w, sms, s)) return rc;
   if (want_pairs) {
     scan_kernel<<<1, 1024, 0, s>>>(counts, n, pair_offsets, pairs_needed, p.cap, status);
     scatter_kernel<<<1024, 256, 0, s>>>(triples, p.pair_count, p.cap, pair_offsets, counts, pairs);
-    if (flags & CBVH_SORT_PAIRS) sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(pair_offsets, n, p.pair_count, p.cap, pairs);
+    if (flags & CBVH_SORT_PAIRS)
+      sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(pair_offsets, n, p.pair_count, p.cap, pairs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "compaction launch");
   }
@@ -1036,23 +1225,26 @@ extern "C" int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *
   cbvh::clear_error();
   if (int rc = check_pair(A, B)) return rc;
   if (n < 0 || (n > 0 && (!poses || !dist)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
-  if (n > 0xffffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
-  if (!workspace || workspace_bytes < ws_bytes(n, 1, 0) || (reinterpret_cast<uintptr_t>(workspace) & 15))
-    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or misaligned");
+  if (n > 0x7fffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
+  int sms = 0;
+  if (int rc = device_sms(&sms)) return rc;
+  Params p;
+  fill_params(p, A, B);
+  const WsPlan w = ws_plan(p.L, n, 1, 0, sms);
+  if (!workspace || workspace_bytes < w.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(workspace, 0, kWsHeader, s);
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  cudaError_t e = cudaMemsetAsync(ws, 0, kWsHeader, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   if (n == 0) return CBVH_OK;
-  Params p;
-  fill_params(p, A, B);
   p.poses = poses;
   p.n = n;
   p.dist = dist;
   p.status = status;
-  p.task_next = static_cast<unsigned int *>(workspace);
-  p.stats = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(workspace) + 16);
-  return launch_traverse<MODE_PQ>(p, s);
+  p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+  return launch_rounds<MODE_PQ>(p, ws, w, sms, s);
 }
 
 extern "C" int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream) {
@@ -1065,10 +1257,27 @@ extern "C" int cbvh_query_stats(const void *workspace, int64_t *stats_host, void
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "cbvh_query_stats");
 }
 
-extern "C" int cbvh_profile_events(void *before, void *after) {
+extern "C" int cbvh_profile_enable(int on) {
   cbvh::clear_error();
-  if ((before == nullptr) != (after == nullptr)) return cbvh::fail(CBVH_ERR_ARG, "give both events or neither");
-  g_prof_before = static_cast<cudaEvent_t>(before);
-  g_prof_after = static_cast<cudaEvent_t>(after);
+  g_prof.on = on != 0;
   return CBVH_OK;
+}
+
+extern "C" int cbvh_profile_collect(double *ms_host, int64_t *launches_host) {
+  cbvh::clear_error();
+  if (!ms_host || !launches_host) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  ms_host[0] = ms_host[1] = 0.0;
+  launches_host[0] = launches_host[1] = 0;
+  int rc = CBVH_OK;
+  for (auto &r : g_prof.used) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cbvh_profile_collect");
+    ms_host[r.mode] += ms;
+    launches_host[r.mode] += 1;
+    g_prof.spare.push_back(r);
+  }
+  g_prof.used.clear();
+  return rc;
 }

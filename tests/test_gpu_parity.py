@@ -246,17 +246,28 @@ def test_c2_full_size_sampled_against_oracle(cb, c2):
     pairs = _pairs_by_pose(res.offsets.cpu().numpy(), res.pairs.cpu().numpy())
     rng = np.random.default_rng(5)
     idx = np.sort(rng.choice(len(P), 48, replace=False))
-    near, _ = oracle.near_contact(c2["Ao"], c2["Bo"], P[idx], EPS_NEAR * c2["D"])
-    keep = idx[~near]
-    assert len(keep) >= 30
-    o_hit, o_off, o_ij, _ = oracle.collide(c2["Ao"], c2["Bo"], P[keep])
+    eps = EPS_NEAR * c2["D"]
+    o_hit, o_off, o_ij, _ = oracle.collide(c2["Ao"], c2["Bo"], P[idx])
     o_pairs = _pairs_by_pose(o_off, o_ij)
-    o_d, _ = oracle.distance(c2["Ao"], c2["Bo"], P[keep])
-    for q, p in enumerate(keep):
-        assert hit[p] == o_hit[q]
-        assert pairs[p].shape == o_pairs[q].shape and (pairs[p] == o_pairs[q]).all()
-    assert np.abs(dist[keep] - o_d).max() <= TOL_PQ * c2["D"]
-    assert o_hit.sum() >= 5 and (o_hit == 0).sum() >= 5
+    n_off, n_ij = oracle.near_pairs(c2["Ao"], c2["Bo"], P[idx], eps)
+    amb = _pairs_by_pose(n_off, n_ij)
+    o_d, _ = oracle.distance(c2["Ao"], c2["Bo"], P[idx])
+    exact_poses = 0
+    for q, p in enumerate(idx):
+        key = lambda a: set(map(tuple, np.asarray(a).tolist()))  # noqa: E731
+        gpu, ora, am = key(pairs[p]), key(o_pairs[q]), key(amb[q])
+        certain = ora - am
+        # unique part: every pair the oracle finds with margin >= eps; the rest must be valid
+        assert certain <= gpu <= (ora | am), (p, len(certain - gpu), len(gpu - (ora | am)))
+        if certain:
+            assert hit[p] == 1
+        if not (ora | am):
+            assert hit[p] == 0
+        if not am:
+            exact_poses += 1
+            assert gpu == ora and hit[p] == o_hit[q]
+    assert np.abs(dist[idx] - o_d).max() <= TOL_PQ * c2["D"]
+    assert o_hit.sum() >= 5 and (o_hit == 0).sum() >= 5 and exact_poses >= 10
     # properties of every pose: hit iff a pair, pairs sorted; hit iff distance 0 except where
     # CD and PQ may round a near-contact pair differently -- every such pose must be one that
     # the oracle flags as near contact
