@@ -125,6 +125,25 @@ int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64
 int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist, void *workspace,
                   int64_t workspace_bytes, int32_t *status, void *stream);
 
+/* Proximity query that allocates nothing and takes no workspace: the same computation and
+ * results as cbvh_distance, for callers that cannot hand the library device memory at
+ * query time -- for example a planner's control loop that must never block on the device
+ * allocator once it runs, or a plug-in whose host application owns all device memory.
+ * The paper has no counterpart; it is a packaging of the same query.
+ *   Scratch: a fixed 32 MiB array inside the library, reserved on every GPU that loads it
+ *   until the process exits.  It holds the query's counters, its task buffers and one
+ *   node-pair stack per warp; pairs of hierarchies whose stack bound leaves room for fewer
+ *   than 4 warps are rejected with CBVH_ERR_WORKSPACE and a message giving the bytes needed.
+ *   The pose count itself is not limited by the array.
+ *   Set-up: the first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   Sharing: every call uses the same array and it keeps the previous call's contents (the
+ *   counters are cleared at the start of each call); calls whose work overlaps on the GPU,
+ *   on different streams or threads, race and give wrong results -- serialise them.
+ *   Arguments, outputs and errors are those of cbvh_distance. */
+int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist,
+                          int32_t *status, void *stream);
+
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests
  * (bounding-volume overlap or lower-bound tests, Algorithm 1's "a and b intersect"),
  * stats_host[1] = leaf tests (checkPrimitives calls).  Copies 16 bytes to the host and

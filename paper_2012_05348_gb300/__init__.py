@@ -49,11 +49,12 @@ def _declare(L):
     L.cbvh_collide.argtypes = [P, P, P, I64, P, P, P, I64, P, U32, P, I64, P, P]
     L.cbvh_distance.argtypes = [P, P, P, I64, P, P, I64, P, P]
     L.cbvh_query_stats.argtypes = [P, P, P]
+    L.cbvh_distance_noalloc.argtypes = [P, P, P, I64, P, P, P]
     L.cbvh_profile_enable.argtypes = [I32]
     L.cbvh_profile_collect.argtypes = [P, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
               "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
-              "cbvh_profile_collect"):
+              "cbvh_profile_collect", "cbvh_distance_noalloc"):
         getattr(L, f).restype = I32
     return L
 

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -1280,4 +1281,97 @@ extern "C" int cbvh_profile_collect(double *ms_host, int64_t *launches_host) {
   }
   g_prof.used.clear();
   return rc;
+}
+
+// ---------------------------------------------------------------- distance without allocation
+// Scratch of cbvh_distance_noalloc: counters, the two task buffers and the per-warp stacks
+// of the proximity query, in one fixed array that every GPU loading this library holds
+// until the process exits.  Calls share it, so calls that overlap on the GPU race.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+constexpr uint32_t kNoAllocTasks = 1u << 17;               // entries per task buffer
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[1024] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+int noalloc_scratch(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 1024) return cbvh::fail(CBVH_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return CBVH_OK;
+}
+}  // namespace
+
+extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist,
+                                     int32_t *status, void *stream) {
+  cbvh::clear_error();
+  if (int rc = check_pair(A, B)) return rc;
+  if (n < 0 || (n > 0 && (!poses || !dist)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
+  if (n > 0x7fffffffll) return cbvh::fail(CBVH_ERR_ARG, "too many poses for one call");
+  void *scratch = nullptr;
+  if (int rc = noalloc_scratch(&scratch)) return rc;
+  int sms = 0;
+  if (int rc = device_sms(&sms)) return rc;
+  Params p;
+  fill_params(p, A, B);
+  // carve the fixed array: counters, two task buffers, then as many warp stacks as fit
+  const int64_t tasks_bytes = 16 * (int64_t)kNoAllocTasks;
+  const int64_t stacks_off = kWsHeader + 2 * tasks_bytes;
+  const int64_t per_warp = 8 * (int64_t)p.L.stack_cap;
+  const int64_t warps_fit = ((int64_t)kNoAllocScratchBytes - stacks_off) / per_warp;
+  if (warps_fit < kWarpsPerBlock)
+    return cbvh::fail(CBVH_ERR_WORKSPACE,
+                      "this pair of hierarchies needs " + std::to_string(per_warp * kWarpsPerBlock + stacks_off) +
+                          " bytes of scratch; cbvh_distance_noalloc has " + std::to_string(kNoAllocScratchBytes));
+  const int smem = kWarpsPerBlock * p.L.warp_bytes;
+  cudaError_t e = cudaFuncSetAttribute(traverse_kernel<MODE_PQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_kernel<MODE_PQ>, kThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
+  const int blocks = (int)std::min<int64_t>((int64_t)sms * std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock),
+                                            warps_fit / kWarpsPerBlock);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t *ws = static_cast<uint8_t *>(scratch);
+  // the counters must start at zero; the task buffers and stacks are written before read
+  e = cudaMemsetAsync(ws, 0, kWsHeader, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (n == 0) return CBVH_OK;
+  p.poses = poses;
+  p.n = n;
+  p.dist = dist;
+  p.status = status;
+  p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+  p.stacks = reinterpret_cast<uint2 *>(ws + stacks_off);
+  p.task_cap = kNoAllocTasks;
+  p.spill_below = (uint32_t)std::min<int64_t>((int64_t)blocks * kWarpsPerBlock * 16, kNoAllocTasks);
+  unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64);
+  unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128);
+  uint4 *buf[2] = {reinterpret_cast<uint4 *>(ws + kWsHeader), reinterpret_cast<uint4 *>(ws + kWsHeader + tasks_bytes)};
+  for (int r = 0; r < kRounds; ++r) {
+    p.round = r;
+    p.last_round = r == kRounds - 1;
+    p.budget = kBudget[r];
+    p.task_next = next + r;
+    p.count_in = count + r;
+    p.count_out = count + r + 1;
+    p.tasks_in = buf[(r + 1) & 1];
+    p.tasks_out = buf[r & 1];
+    traverse_kernel<MODE_PQ><<<blocks, kThreads, smem, s>>>(p);
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "traverse launch");
 }
