@@ -228,8 +228,8 @@ def main():
     torch.cuda.synchronize()
     if int(st_cd.item()) or int(st_pq.item()):
         raise RuntimeError(f"device status {int(st_cd.item())} / {int(st_pq.item())}")
-    bv_cd, leaf_cd = cb.query_stats(ws_cd)
-    bv_pq, leaf_pq = cb.query_stats(ws_pq)
+    bv_cd, leaf_cd, exp_cd = cb.query_stats(ws_cd)
+    bv_pq, leaf_pq, exp_pq = cb.query_stats(ws_pq)
     n_pairs = int(need.item())
 
     # ---- timed: device-resident inputs; L2 flushed (untimed) before every step ----
@@ -299,7 +299,7 @@ def main():
     cd_bytes = bv_cd * BYTES_BV + leaf_cd * BYTES_LEAF + n * BYTES_POSE + n_pairs * 3 * 4
     pq_bytes = bv_pq * BYTES_BV + leaf_pq * BYTES_LEAF + n * BYTES_POSE
     cd_avg = prof["collide"][0] / max(1, prof["collide"][1])
-    pq_avg = prof["distance"][0] / max(1, prof["distance"][1])
+    pq_avg = prof["distance"][0] / max(1, prof["distance"][1] // 2)  # two passes per distance query
     dom = ("traverse_kernel<CD>", cd_bytes, cd_avg) if cd_avg >= pq_avg else ("traverse_kernel<PQ>", pq_bytes, pq_avg)
     achieved = dom[1] / (dom[2] / 1e3) / 1e9
     traffic = None
@@ -328,6 +328,8 @@ def main():
         "pq_pose_queries_per_s": n / (pq_avg / 1e3),
         "bv_pair_tests_per_s": (bv_cd + bv_pq) * K / (total_ms / 1e3),
         "bv_pair_tests_per_step": bv_cd + bv_pq, "leaf_tests_per_step": leaf_cd + leaf_pq,
+        "work_per_step": {"cd": {"bv_tests": bv_cd, "leaf_tests": leaf_cd, "expansions": exp_cd},
+                          "pq": {"bv_tests": bv_pq, "leaf_tests": leaf_pq, "expansions": exp_pq}},
         "pairs_per_step": n_pairs,
         "latency_ms": {"p50": sm[len(sm) // 2], "p99": sm[min(len(sm) - 1, int(round(0.99 * (len(sm) - 1))))],
                        "per": f"step of {n} poses (one CD + one PQ launch group)"},
@@ -335,7 +337,8 @@ def main():
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_source": f"{peak_src} HBM copy bandwidth",
                      "bytes": "algorithmic: BV tests x 34 B + leaf tests x 72 B + poses x 61 B (+ 12 B per pair)"},
-        "kernel_ms": {"traverse_cd": cd_avg, "traverse_pq": pq_avg},
+        "kernel_ms": {"traverse_cd": cd_avg, "traverse_pq": pq_avg,
+                      "compaction": prof["compaction"][0] / max(1, prof["compaction"][1])},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "pose queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),

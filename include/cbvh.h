@@ -121,7 +121,8 @@ int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64
 
 /* Proximity query: dist[p] = minimum distance between the triangles of A and those of
  * R_p B + t_p (0 when they intersect), by branch-and-bound Algorithm 1 with slab-gap lower
- * bounds.  FP32; accurate to a few ulps of the scene size. */
+ * bounds.  A collision pass with early exit runs first and settles the intersecting poses
+ * at 0.  FP32; accurate to a few ulps of the scene size. */
 int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist, void *workspace,
                   int64_t workspace_bytes, int32_t *status, void *stream);
 
@@ -146,18 +147,23 @@ int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const float *pos
 
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests
  * (bounding-volume overlap or lower-bound tests, Algorithm 1's "a and b intersect"),
- * stats_host[1] = leaf tests (checkPrimitives calls).  Copies 16 bytes to the host and
- * synchronises `stream`.  The paper has no such call; it feeds the BV-pair tests/s metric. */
+ * stats_host[1] = leaf tests (checkPrimitives calls), stats_host[2] = node-pair expansions
+ * (one per recursive call of Algorithm 1 that reaches an inner node).  Copies 24 bytes to
+ * the host and synchronises `stream`.  The paper has no such call; it feeds the BV-pair
+ * tests/s metric. */
 int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream);
 
-/* Profiling of the traversal kernel alone.  While enabled (on != 0), every query on this
- * host thread records a pair of library-owned CUDA events on its stream immediately around
- * its traversal kernel.  The paper has no such call; it feeds the roofline measurement. */
+/* Profiling of the traversal kernels alone.  While enabled (on != 0), every query on this
+ * host thread records pairs of library-owned CUDA events on its stream immediately around
+ * its traversal launches and its output compaction.  The paper has no such call; it feeds
+ * the roofline measurement. */
 int cbvh_profile_enable(int on);
 
-/* Waits for the recorded event pairs of this host thread and returns, per mode (index 0 =
- * collide, 1 = distance), the summed traversal-kernel time in ms (ms_host[2]) and the
- * number of launches (launches_host[2]); then forgets them. */
+/* Waits for the recorded event pairs of this host thread and returns, per slot, the summed
+ * time in ms (ms_host[3]) and the number of timed launch groups (launches_host[3]; a
+ * distance query has two, one per pass): slot 0 = the
+ * traversal kernels of collide, 1 = those of distance (both of its passes), 2 = collide's
+ * output compaction (scan, scatter, sort); then forgets them. */
 int cbvh_profile_collect(double *ms_host, int64_t *launches_host);
 
 #ifdef __cplusplus

@@ -206,10 +206,10 @@ def collide(A: BVH, B: BVH, poses, *, pairs: bool = True, sort: bool = True, ear
 
 
 def query_stats(workspace, stream=None):
-    """(BV-pair tests, leaf tests) of the last query that used this workspace tensor."""
-    out = np.zeros(2, np.int64)
+    """(BV-pair tests, leaf tests, expansions) of the last query that used this workspace."""
+    out = np.zeros(3, np.int64)
     _check(_load().cbvh_query_stats(_ptr(workspace), out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def profile_enable(on: bool = True):
@@ -218,11 +218,12 @@ def profile_enable(on: bool = True):
 
 
 def profile_collect():
-    """{'collide': (ms, launches), 'distance': (ms, launches)} since the last collect."""
-    ms = np.zeros(2)
-    n = np.zeros(2, np.int64)
+    """{'collide' | 'distance' | 'compaction': (ms, queries)} since the last collect."""
+    ms = np.zeros(3)
+    n = np.zeros(3, np.int64)
     _check(_load().cbvh_profile_collect(ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
-    return {"collide": (float(ms[0]), int(n[0])), "distance": (float(ms[1]), int(n[1]))}
+    return {"collide": (float(ms[0]), int(n[0])), "distance": (float(ms[1]), int(n[1])),
+            "compaction": (float(ms[2]), int(n[2]))}
 
 
 def distance(A: BVH, B: BVH, poses, *, stream=None, check: bool = True):

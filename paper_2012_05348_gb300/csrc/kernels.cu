@@ -40,6 +40,9 @@ constexpr int kMaxM = 16;   // branching factor
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = 32 * kWarpsPerBlock;
+#ifndef CBVH_MIN_BLOCKS
+#define CBVH_MIN_BLOCKS 1
+#endif
 
 __constant__ int c_dir[kMaxK][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
                                     {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
@@ -82,10 +85,10 @@ struct Params {
   float *dist;
   // common
   int32_t *status;
-  unsigned long long *stats;  // [0] BV-pair tests, [1] leaf tests (checkPrimitives calls)
+  unsigned long long *stats;  // [0] BV-pair tests, [1] leaf tests (checkPrimitives calls), [2] expansions
+  const uint8_t *skip;        // PQ: poses already known to intersect (distance 0), or null
   // rounds
   int round, last_round, budget;
-  uint32_t spill_below;       // a round hands work on only while it has fewer tasks than this
   uint32_t task_cap;
   unsigned int *task_next;    // this round's task cursor
   const unsigned int *count_in;
@@ -197,7 +200,7 @@ __device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int la
 // (row stride KS), references to ref[], and leaf slots (or 0xffffffff) to leaf[].  Returns
 // the number of members (warp-uniform).
 __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float *lo, float *hi, int KS,
-                          uint32_t *ref, uint32_t *leaf) {
+                          uint32_t *ref, uint32_t *leaf, bool leaf_bounds = true) {
   const uint32_t t = x >> X.lbits;
   if (t != S.cur_t) {
     S.cur_t = t;
@@ -209,6 +212,14 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
   const bool ext = (w0 >> 21) & 1u;
   const bool self = force_self || nc == 0;
   const int nd = S.nd;
+  if (self && nc == 0 && !leaf_bounds) {  // a leaf standing for itself, bounded by its triangle
+    if (lane == 0) {
+      ref[0] = x;
+      leaf[0] = w1;
+    }
+    __syncwarp();
+    return 1;
+  }
   if (X.bits == 0) {
     if (self) {
       if (lane < nd) {
@@ -494,9 +505,10 @@ __device__ __forceinline__ float2 project_member(const Params &p, const float *q
 // A warp runs Algorithm 1 depth-first from its task with an explicit stack; in a round that
 // may hand work on, a task that has used its expansion budget moves its whole stack into
 // the next round's task buffer, so that the node-pair tree of a heavy pose is spread over
-// many warps.  The last round has no budget and finishes every task.
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
+// many warps.  The last round has no budget and finishes every task; when a task buffer is
+// full, warps simply keep their work.
+template <int MODE, int KA>
+__global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(const Params p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -504,7 +516,7 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
   uint2 *stack = p.stacks + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * (size_t)p.L.stack_cap;
   uint2 *leafq = reinterpret_cast<uint2 *>(ws + p.L.o_leafq);
   float *pc = reinterpret_cast<float *>(ws + p.L.o_pose);
-  const int KA = p.A.K, KS = p.L.KS;
+  constexpr int KS = (KA & 1) ? KA : KA + 1;
   Side SA{reinterpret_cast<uint32_t *>(ws + p.L.o_tagA), reinterpret_cast<int2 *>(ws + p.L.o_latA),
           reinterpret_cast<int *>(ws + p.L.o_pathA), KA, 0xffffffffu, nullptr};
   Side SB{reinterpret_cast<uint32_t *>(ws + p.L.o_tagB), reinterpret_cast<int2 *>(ws + p.L.o_latB),
@@ -525,9 +537,11 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
   const bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t n_in = p.round == 0 ? (uint32_t)p.n : min(*p.count_in, p.task_cap);
-  const bool may_spill = !p.last_round && n_in < p.spill_below;
-  unsigned long long n_bv = 0, n_leaf = 0;
+  const bool may_spill = !p.last_round;
+  unsigned long long n_bv = 0, n_leaf = 0, n_exp = 0;
   int64_t cur_pose = -1;
+  uint32_t keyA = 0xffffffffu, keyB = 0xffffffffu;  // node whose member set is decoded / projected
+  int na_c = 0, nb_c = 0;
 
   for (;;) {
     unsigned int task = 0;
@@ -548,6 +562,7 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
       root = false;
     }
     if ((int64_t)pose != cur_pose) {
+      keyB = 0xffffffffu;  // projections depend on the pose
       // ---- pose precompute: u_j = R^T d_j, |u_j|, [s_lo, s_hi] of d_j.t, and eta_j, a
       // bound on the rounding error of each component of u_j ----
       cur_pose = pose;
@@ -574,6 +589,10 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
     // per-pose state: the root task initialises it; later tasks update it atomically
     float best = INFINITY;
     if (root) {
+      if (MODE == MODE_PQ && p.skip && p.skip[pose]) {  // intersecting: the distance is 0
+        if (lane == 0) p.dist[pose] = 0.f;
+        continue;
+      }
       if (lane == 0) {
         if (MODE == MODE_CD) {
           p.hit[pose] = 0;
@@ -647,17 +666,33 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
 
     for (;;) {
       // ---------------- expand (a, b) as Algorithm 1 does ----------------
-      const int na = decode_set(p.A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
-      const int nb = decode_set(p.B, SB, b, root, lane, blo, bhi, 4, bref, bleaf);
+      // A's member set depends on a only, B's projected set on b and the pose: in depth-first
+      // order one of them is often the same as in the previous expansion and is reused.
+      int na, nb;
+      if (a != keyA || root) {
+        na = decode_set(p.A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
+        keyA = root ? 0xffffffffu : a;
+        na_c = na;
+      } else {
+        na = na_c;
+      }
+      if (b != keyB || root) {
+        nb = decode_set(p.B, SB, b, root, lane, blo, bhi, 4, bref, bleaf, false);
+        for (int it = lane; it < nb * KA; it += 32) {
+          const int i = it / KA, j = it - i * KA;
+          const float2 r = project_member(p, pose_dir(pc, j), blo, bhi, bleaf[i], i);
+          plo[i * KS + j] = r.x;
+          phi[i * KS + j] = r.y;
+        }
+        __syncwarp();
+        keyB = root ? 0xffffffffu : b;
+        nb_c = nb;
+      } else {
+        nb = nb_c;
+      }
       root = false;
       ++expansions;
-      for (int it = lane; it < nb * KA; it += 32) {
-        const int i = it / KA, j = it - i * KA;
-        const float2 r = project_member(p, pose_dir(pc, j), blo, bhi, bleaf[i], i);
-        plo[i * KS + j] = r.x;
-        phi[i * KS + j] = r.y;
-      }
-      __syncwarp();
+      ++n_exp;
       // test every member pair; survivors are compacted by ballot onto the stack (inner
       // pairs) or the leaf queue (leaf pairs)
       const int np = na * nb;
@@ -675,9 +710,11 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
           const float *al = alo + i * KS, *ah = ahi + i * KS, *pl = plo + j * KS, *ph = phi + j * KS;
           if (MODE == MODE_CD) {
             keep = true;
+#pragma unroll
             for (int d = 0; d < KA; ++d) keep &= (al[d] <= ph[d]) & (pl[d] <= ah[d]);
           } else {
             lb = 0.f;
+#pragma unroll
             for (int d = 0; d < KA; ++d) {
               const float g = fmaxf(__fsub_rd(al[d], ph[d]), __fsub_rd(pl[d], ah[d]));
               lb = fmaxf(lb, __fmul_rd(g, p.invn[d]));
@@ -717,6 +754,8 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
         sp += __popc(mi);
         __syncwarp();
         while (nleaf >= 32 && !done) drain(32);
+        // PQ: until some distance is known nothing can be pruned, so test leaf pairs at once
+        if (MODE == MODE_PQ && nleaf > 0 && best == INFINITY && !done) drain(nleaf);
       }
       // PQ: the most promising child pair goes on top, so that it is expanded next
       if (MODE == MODE_PQ && run_pos >= 0 && run_pos != sp - 1 && !done) {
@@ -791,6 +830,7 @@ __global__ void __launch_bounds__(kThreads) traverse_kernel(const Params p) {
   if (lane == 0) {
     atomicAdd(&p.stats[0], n_bv);
     atomicAdd(&p.stats[1], n_leaf);
+    atomicAdd(&p.stats[2], n_exp);
   }
 }
 
@@ -1019,15 +1059,16 @@ thread_local Profiler g_prof;
 
 // Rounds of a query and the expansion budget of a task in each (0 = none, last round).
 constexpr int kRounds = 6;
-constexpr int kBudget[kRounds] = {16, 32, 64, 128, 256, 0};
+constexpr int kBudget[kRounds] = {16, 32, 64, 128, 512, 0};
 constexpr int kMaxWarpsPerSM = 64;
 
-// Workspace layout: [0, 256) counters -- u64 pair count at 0, u64 stats[2] at 16, u32 task
-// cursor per round at 64, u32 task count per round at 128 -- then the per-pose pair counts
-// and (pose, i, j) triples (collide with pairs), two task buffers and the per-warp stacks.
+// Workspace layout: [0, 256) counters -- u64 pair count at 0, u64 stats[3] at 16, u32 task
+// cursor per round at 64, u32 task count per round at 128 (one block of cursors and counts
+// per pass) -- then the per-pose pair counts and (pose, i, j) triples (collide with pairs),
+// per-pose intersection flags (distance), two task buffers and the per-warp stacks.
 constexpr int64_t kWsHeader = 256;
 struct WsPlan {
-  int64_t counts, triples, tasks0, tasks1, stacks, total;
+  int64_t counts, triples, flags, tasks0, tasks1, stacks, total;
   uint32_t task_cap;
   int warps_max;
 };
@@ -1039,6 +1080,8 @@ WsPlan ws_plan(const Layout &L, int64_t n, int mode, int64_t cap, int sms) {
   if (mode == 0) o = align256(o + 4 * n);
   w.triples = o;
   if (mode == 0) o = align256(o + 12 * std::max<int64_t>(cap, 0));
+  w.flags = o;
+  if (mode == 1) o = align256(o + n);
   const int64_t tcap = std::min<int64_t>(std::max<int64_t>(int64_t(1) << 20, 256 * n), int64_t(1) << 30);
   w.task_cap = (uint32_t)tcap;
   w.tasks0 = o;
@@ -1059,29 +1102,41 @@ int device_sms(int *sms) {
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "device query");
 }
 
+// The traversal kernel compiled for A's number of slab directions (k = 6, 18, 24, 26).
+typedef void (*TraverseFn)(const Params);
 template <int MODE>
-int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t s) {
+TraverseFn traverse_fn(int K) {
+  switch (K) {
+    case 3: return traverse_kernel<MODE, 3>;
+    case 9: return traverse_kernel<MODE, 9>;
+    case 12: return traverse_kernel<MODE, 12>;
+    default: return traverse_kernel<MODE, 13>;
+  }
+}
+
+template <int MODE>
+int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t s, int pass = 0, int slot = MODE) {
   const int smem = kWarpsPerBlock * p.L.warp_bytes;
-  cudaError_t e = cudaFuncSetAttribute(traverse_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const TraverseFn fn = traverse_fn<MODE>(p.A.K);
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_kernel<MODE>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
   per_sm = std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock);
   const int blocks = sms * per_sm;
-  unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64);
-  unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128);
+  unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64) + 8 * pass;
+  unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128) + 8 * pass;
   uint4 *buf[2] = {reinterpret_cast<uint4 *>(ws + w.tasks0), reinterpret_cast<uint4 *>(ws + w.tasks1)};
   p.stacks = reinterpret_cast<uint2 *>(ws + w.stacks);
   p.task_cap = w.task_cap;
-  p.spill_below = (uint32_t)std::min<int64_t>((int64_t)blocks * kWarpsPerBlock * 16, w.task_cap);
-  ProfRec rec{nullptr, nullptr, MODE};
+  ProfRec rec{nullptr, nullptr, slot};
   if (g_prof.on) {
     if (!g_prof.spare.empty()) {
       rec = g_prof.spare.back();
       g_prof.spare.pop_back();
-      rec.mode = MODE;
+      rec.mode = slot;
     } else if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess) {
       return cbvh::fail(CBVH_ERR_CUDA, "cudaEventCreate");
     }
@@ -1096,7 +1151,7 @@ int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t
     p.count_out = count + r + 1;
     p.tasks_in = buf[(r + 1) & 1];
     p.tasks_out = buf[r & 1];
-    traverse_kernel<MODE><<<blocks, kThreads, smem, s>>>(p);
+    fn<<<blocks, kThreads, smem, s>>>(p);
   }
   e = cudaGetLastError();
   if (g_prof.on) {
@@ -1211,11 +1266,26 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
   }
   if (int rc = launch_rounds<MODE_CD>(p, ws, w, sms, s)) return rc;
   if (want_pairs) {
+    ProfRec rec{nullptr, nullptr, 2};
+    if (g_prof.on) {
+      if (!g_prof.spare.empty()) {
+        rec = g_prof.spare.back();
+        g_prof.spare.pop_back();
+        rec.mode = 2;
+      } else if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess) {
+        return cbvh::fail(CBVH_ERR_CUDA, "cudaEventCreate");
+      }
+      cudaEventRecord(rec.a, s);
+    }
     scan_kernel<<<1, 1024, 0, s>>>(counts, n, pair_offsets, pairs_needed, p.cap, status);
     scatter_kernel<<<1024, 256, 0, s>>>(triples, p.pair_count, p.cap, pair_offsets, counts, pairs);
     if (flags & CBVH_SORT_PAIRS)
       sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(pair_offsets, n, p.pair_count, p.cap, pairs);
     e = cudaGetLastError();
+    if (g_prof.on) {
+      cudaEventRecord(rec.b, s);
+      g_prof.used.push_back(rec);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "compaction launch");
   }
   return CBVH_OK;
@@ -1240,19 +1310,33 @@ extern "C" int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   if (n == 0) return CBVH_OK;
+  // Pass 1: collision detection with early exit marks the poses whose distance is 0.
+  // Pass 2: branch and bound on the others.  Distance 0 iff the meshes intersect, and both
+  // passes decide intersection with the same triangle test, so the result is that of a
+  // single branch-and-bound pass; pass 1 only finds the zeros sooner.
+  Params q = p;
+  q.poses = poses;
+  q.n = n;
+  q.hit = ws + w.flags;
+  q.flags = CBVH_EARLY_EXIT;
+  q.status = status;
+  q.pair_count = reinterpret_cast<unsigned long long *>(ws);
+  q.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+  if (int rc = launch_rounds<MODE_CD>(q, ws, w, sms, s, 0, 1)) return rc;
   p.poses = poses;
   p.n = n;
   p.dist = dist;
   p.status = status;
+  p.skip = ws + w.flags;
   p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
-  return launch_rounds<MODE_PQ>(p, ws, w, sms, s);
+  return launch_rounds<MODE_PQ>(p, ws, w, sms, s, 1);
 }
 
 extern "C" int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream) {
   cbvh::clear_error();
   if (!workspace || !stats_host) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(stats_host, static_cast<const uint8_t *>(workspace) + 16, 2 * sizeof(int64_t),
+  cudaError_t e = cudaMemcpyAsync(stats_host, static_cast<const uint8_t *>(workspace) + 16, 3 * sizeof(int64_t),
                                   cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "cbvh_query_stats");
@@ -1267,8 +1351,8 @@ extern "C" int cbvh_profile_enable(int on) {
 extern "C" int cbvh_profile_collect(double *ms_host, int64_t *launches_host) {
   cbvh::clear_error();
   if (!ms_host || !launches_host) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
-  ms_host[0] = ms_host[1] = 0.0;
-  launches_host[0] = launches_host[1] = 0;
+  ms_host[0] = ms_host[1] = ms_host[2] = 0.0;
+  launches_host[0] = launches_host[1] = launches_host[2] = 0;
   int rc = CBVH_OK;
   for (auto &r : g_prof.used) {
     float ms = 0.f;
@@ -1335,10 +1419,11 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
                       "this pair of hierarchies needs " + std::to_string(per_warp * kWarpsPerBlock + stacks_off) +
                           " bytes of scratch; cbvh_distance_noalloc has " + std::to_string(kNoAllocScratchBytes));
   const int smem = kWarpsPerBlock * p.L.warp_bytes;
-  cudaError_t e = cudaFuncSetAttribute(traverse_kernel<MODE_PQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const TraverseFn fn = traverse_fn<MODE_PQ>(p.A.K);
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_kernel<MODE_PQ>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
   const int blocks = (int)std::min<int64_t>((int64_t)sms * std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock),
@@ -1357,7 +1442,6 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
   p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
   p.stacks = reinterpret_cast<uint2 *>(ws + stacks_off);
   p.task_cap = kNoAllocTasks;
-  p.spill_below = (uint32_t)std::min<int64_t>((int64_t)blocks * kWarpsPerBlock * 16, kNoAllocTasks);
   unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64);
   unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128);
   uint4 *buf[2] = {reinterpret_cast<uint4 *>(ws + kWsHeader), reinterpret_cast<uint4 *>(ws + kWsHeader + tasks_bytes)};
@@ -1370,7 +1454,7 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
     p.count_out = count + r + 1;
     p.tasks_in = buf[(r + 1) & 1];
     p.tasks_out = buf[r & 1];
-    traverse_kernel<MODE_PQ><<<blocks, kThreads, smem, s>>>(p);
+    fn<<<blocks, kThreads, smem, s>>>(p);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "traverse launch");
