@@ -145,6 +145,45 @@ int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int6
 int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist,
                           int32_t *status, void *stream);
 
+/* ---- batched queries (one pass of persistent launches over many work items) ----
+ * A work item pairs a static hierarchy A with a posed hierarchy B for n poses and asks for
+ * collision flags (mode 0; flags CBVH_EARLY_EXIT or 0) or distances (mode 1).  Items that
+ * share the query kind and A's k run in one set of persistent launches, so items of very
+ * different sizes (robot links against a scene, many requests) share the GPU.  Outputs and
+ * semantics per item are those of cbvh_collide without pairs and of cbvh_distance. */
+typedef struct {
+  const cbvh_bvh *A;  /* static side (attached) */
+  const cbvh_bvh *B;  /* posed side (attached) */
+  int32_t mode;       /* 0 = collision detection, 1 = proximity query */
+  uint32_t flags;     /* mode 0: CBVH_EARLY_EXIT or 0; mode 1: 0 */
+  const float *poses; /* device, n x 12 */
+  int64_t n;
+  uint8_t *hit;       /* device, n bytes (mode 0) */
+  float *dist;        /* device, n floats (mode 1) */
+} cbvh_query_t;
+
+typedef struct cbvh_batch cbvh_batch; /* opaque host-side plan of a batch */
+
+/* Plan a batch (host only; queries_host is copied).  Errors: CBVH_ERR_ARG, CBVH_ERR_STATE. */
+int cbvh_batch_create(const cbvh_query_t *queries_host, int64_t n_queries, cbvh_batch **out);
+int cbvh_batch_free(cbvh_batch *b);
+/* Device workspace bytes the batch needs (256-byte aligned). */
+int cbvh_batch_workspace_bytes(const cbvh_batch *b, int64_t *bytes);
+/* Write the batch's item table into the workspace (copies and synchronises `stream`). */
+int cbvh_batch_upload(const cbvh_batch *b, void *workspace, int64_t workspace_bytes, void *stream);
+/* Enqueue the batch on `stream`: memsets and kernel launches only, no synchronisation and
+ * no host copies, so the call can be captured in a CUDA graph and replayed (the poses and
+ * outputs named at cbvh_batch_create are read and written at each replay).  Requires a
+ * previous cbvh_batch_upload into the same workspace.  Device errors go to `status`. */
+int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_bytes, int32_t *status, void *stream);
+
+/* Process-wide tuning options; the paper has no counterpart.
+ *   CBVH_OPT_STAGE_BYTES: bytes of leading treelets of each hierarchy that every thread block
+ *   copies into shared memory (TMA bulk copy) before a single query, 0..32768 (default
+ *   16384; 0 disables).  Takes effect for queries issued afterwards. */
+#define CBVH_OPT_STAGE_BYTES 1
+int cbvh_set_option(int option, int64_t value);
+
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests
  * (bounding-volume overlap or lower-bound tests, Algorithm 1's "a and b intersect"),
  * stats_host[1] = leaf tests (checkPrimitives calls), stats_host[2] = node-pair expansions

@@ -18,8 +18,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["BVH", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect", "CbvhError", "lib",
-           "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
+__all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
+           "set_option", "OPT_STAGE_BYTES", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
 LIB_PATH = _build.LIB
 EARLY_EXIT = 1
@@ -50,11 +50,18 @@ def _declare(L):
     L.cbvh_distance.argtypes = [P, P, P, I64, P, P, I64, P, P]
     L.cbvh_query_stats.argtypes = [P, P, P]
     L.cbvh_distance_noalloc.argtypes = [P, P, P, I64, P, P, P]
+    L.cbvh_batch_create.argtypes = [P, I64, C.POINTER(P)]
+    L.cbvh_batch_free.argtypes = [P]
+    L.cbvh_batch_workspace_bytes.argtypes = [P, C.POINTER(I64)]
+    L.cbvh_batch_upload.argtypes = [P, P, I64, P]
+    L.cbvh_batch_launch.argtypes = [P, P, I64, P, P]
+    L.cbvh_set_option.argtypes = [I32, I64]
     L.cbvh_profile_enable.argtypes = [I32]
     L.cbvh_profile_collect.argtypes = [P, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
               "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
-              "cbvh_profile_collect", "cbvh_distance_noalloc"):
+              "cbvh_profile_collect", "cbvh_distance_noalloc", "cbvh_batch_create", "cbvh_batch_free",
+              "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option"):
         getattr(L, f).restype = I32
     return L
 
@@ -153,6 +160,73 @@ class BVH:
     def close(self):
         if getattr(self, "_h", None):
             _load().cbvh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+OPT_STAGE_BYTES = 1
+
+
+def set_option(option: int, value: int) -> None:
+    """cbvh_set_option: process-wide tuning options (OPT_STAGE_BYTES)."""
+    _check(_load().cbvh_set_option(int(option), int(value)))
+
+
+class _Query(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("B", C.c_void_p), ("mode", C.c_int32), ("flags", C.c_uint32),
+                ("poses", C.c_void_p), ("n", C.c_int64), ("hit", C.c_void_p), ("dist", C.c_void_p)]
+
+
+class Batch:
+    """A batched query (cbvh_batch_*): many (A, B, kind, poses) work items run in one set of
+    persistent launches.  Each item is a dict with keys A, B (BVH), kind ('collide' or
+    'distance'), poses (device float32 (n, 12)) and, for collisions, early_exit (bool).
+    Outputs are allocated here: ``outputs[i]`` is uint8 hit flags or float32 distances.
+    ``launch()`` only enqueues work on the stream, so it can be captured in a CUDA graph."""
+
+    def __init__(self, items, device="cuda"):
+        torch = _torch()
+        self.items = items
+        self.outputs = []
+        arr = (_Query * max(1, len(items)))()
+        for i, it in enumerate(items):
+            poses = it["poses"]
+            n = int(poses.shape[0])
+            kind = 1 if it["kind"] == "distance" else 0
+            if kind == 0:
+                out = torch.empty(n, dtype=torch.uint8, device=device)
+                arr[i] = _Query(it["A"].handle, it["B"].handle, 0, EARLY_EXIT if it.get("early_exit") else 0,
+                                poses.data_ptr(), n, out.data_ptr(), None)
+            else:
+                out = torch.empty(n, dtype=torch.float32, device=device)
+                arr[i] = _Query(it["A"].handle, it["B"].handle, 1, 0, poses.data_ptr(), n, None, out.data_ptr())
+            self.outputs.append(out)
+        self._arr = arr
+        h = C.c_void_p()
+        _check(_load().cbvh_batch_create(arr, len(items), C.byref(h)))
+        self._h = h
+        nb = C.c_int64()
+        _check(_load().cbvh_batch_workspace_bytes(h, C.byref(nb)))
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        _check(_load().cbvh_batch_upload(h, _ptr(self.workspace), nb.value, _stream_ptr(None)))
+
+    def launch(self, stream=None):
+        _check(_load().cbvh_batch_launch(self._h, _ptr(self.workspace), self.workspace.numel(), _ptr(self.status),
+                                         _stream_ptr(stream)))
+
+    def run(self, stream=None):
+        self.launch(stream)
+        code = int(self.status.item())
+        if code != 0:
+            raise CbvhError(code, "device status")
+        return self.outputs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().cbvh_batch_free(self._h)
             self._h = None
 
     def __del__(self):

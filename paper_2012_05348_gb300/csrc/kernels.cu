@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -60,18 +61,35 @@ struct BVd {
 
 // Per-warp shared-memory layout (byte offsets inside the warp's slice).
 struct Layout {
+  int tdA, tdB;  // deepest node below a treelet root, A and B (sizes the decode caches)
+  // CTA region: staged treelets of A and B, their offset prefixes, one mbarrier
+  int cta_bytes;
+  int st_off[2], st_bytes[2], st_cnt[2], st_toff[2], o_bar;
   int warp_bytes;
   int o_stack, stack_cap;
   int o_leafq, leafq_cap;
   int o_pose;
   int o_tagA, o_latA, o_pathA;
   int o_tagB, o_latB, o_pathB;
-  int o_aset, o_bset;
+  int o_aset, o_bset, o_bvd;
   int KS;  // row stride (floats) of the per-child direction arrays
+};
+
+// One work item of a batched query (see cbvh_batch_*): a pair of hierarchies, its poses and
+// outputs.  Items of one launch share A's direction count and the query kind.
+struct BatchItem {
+  BVd A, B;
+  const float *poses;
+  uint8_t *hit;
+  float *dist;
+  uint32_t flags, pad;
 };
 
 struct Params {
   BVd A, B;
+  const BatchItem *items;              // batched query: item table, or null
+  const unsigned long long *item_base; // first global pose id of each item, n_items + 1 entries
+  int n_items;
   const float *poses;
   int64_t n;
   // CD
@@ -143,7 +161,22 @@ struct Side {
   int nd;          // directions kept (K for A, 3 for B)
   uint32_t cur_t;  // treelet whose base is cached
   const uint8_t *cur_base;
+  // treelets [0, st_cnt) are staged in shared memory (see stage_treelets); st_off / st_toff
+  // locate the copy and its offset prefix in the dynamic shared memory
+  uint32_t st_cnt;
+  int st_off, st_toff;
 };
+
+extern __shared__ __align__(128) uint8_t g_dsmem[];
+
+// Base of treelet t: its staged copy in shared memory when there is one, else global memory.
+__device__ __forceinline__ const uint8_t *tbase(const BVd &X, const Side &S, uint32_t t) {
+  if (t < S.st_cnt) {
+    const unsigned long long *to = reinterpret_cast<const unsigned long long *>(g_dsmem + S.st_toff);
+    return g_dsmem + S.st_off + (to[t] - to[0]);
+  }
+  return X.blob + X.toff[t];
+}
 
 // Decoded lattice interval of node x for direction j (lanes j < nd).  Walks up to the
 // deepest cached ancestor (or the treelet root), then applies the correctors down to x,
@@ -152,7 +185,7 @@ __device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int la
   const uint32_t t = x >> X.lbits, l = x & X.lmask;
   if (t != S.cur_t) {
     S.cur_t = t;
-    S.cur_base = treelet_base(X, t);
+    S.cur_base = tbase(X, S, t);
   }
   const uint8_t *rx = rec_at(X, S.cur_base, l);
   uint32_t w = ld32(rx);
@@ -204,7 +237,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
   const uint32_t t = x >> X.lbits;
   if (t != S.cur_t) {
     S.cur_t = t;
-    S.cur_base = treelet_base(X, t);
+    S.cur_base = tbase(X, S, t);
   }
   const uint8_t *rx = rec_at(X, S.cur_base, x & X.lmask);
   const uint32_t w0 = ld32(rx), w1 = ld32(rx + 4);
@@ -238,7 +271,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
         uint32_t cref;
         if (ext) {
           cref = (w1 + i) << X.lbits;
-          rc = rec_at(X, treelet_base(X, w1 + i), 0);
+          rc = rec_at(X, tbase(X, S, w1 + i), 0);
         } else {
           cref = (t << X.lbits) | (w1 + i);
           rc = rec_at(X, S.cur_base, w1 + i);
@@ -281,7 +314,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     int2 L;
     if (ext) {
       cref = (w1 + i) << X.lbits;
-      rc = rec_at(X, treelet_base(X, w1 + i), 0);
+      rc = rec_at(X, tbase(X, S, w1 + i), 0);
       L = abs_lattice(rc, j);
     } else {
       cref = (t << X.lbits) | (w1 + i);
@@ -440,10 +473,10 @@ __device__ float tri_dist(const V3 *P, const V3 *Q) {
 
 // Load leaf triangles: A's as stored, B's moved by the pose; both shifted so that A's first
 // vertex is the origin.  Returns the original triangle indices.
-__device__ __forceinline__ void load_pair(const Params &p, const float *pose, uint32_t sa, uint32_t sb, V3 *P, V3 *Q,
-                                          uint32_t &ia, uint32_t &ib) {
-  const float4 a0 = p.A.tris[3 * sa], a1 = p.A.tris[3 * sa + 1], a2 = p.A.tris[3 * sa + 2];
-  const float4 b0 = p.B.tris[3 * sb], b1 = p.B.tris[3 * sb + 1], b2 = p.B.tris[3 * sb + 2];
+__device__ __forceinline__ void load_pair(const float4 *atris, const float4 *btris, const float *pose, uint32_t sa,
+                                          uint32_t sb, V3 *P, V3 *Q, uint32_t &ia, uint32_t &ib) {
+  const float4 a0 = atris[3 * sa], a1 = atris[3 * sa + 1], a2 = atris[3 * sa + 2];
+  const float4 b0 = btris[3 * sb], b1 = btris[3 * sb + 1], b2 = btris[3 * sb + 2];
   ia = __float_as_uint(a0.w);
   ib = __float_as_uint(b0.w);
   const V3 o = {a0.x, a0.y, a0.z};
@@ -466,13 +499,14 @@ enum { MODE_CD = 0, MODE_PQ = 1 };
 // Pose cache layout (floats): R[9], t[3], then per A-direction j: u[3], |u|[3], s_lo, s_hi, eta
 constexpr int kPoseJ = 9;
 __device__ __forceinline__ float *pose_dir(float *pc, int j) { return pc + 12 + kPoseJ * j; }
+constexpr int kStageBytesDefault = 16384;  // per hierarchy and block: leading treelets staged in shared memory
 
 // Conservative interval of d_j . (R x + t) over B-member i: the exact posed triangle when the
 // member is a leaf, otherwise its decoded axis box.  q = pose_dir(pc, j).
-__device__ __forceinline__ float2 project_member(const Params &p, const float *q, const float *blo,
+__device__ __forceinline__ float2 project_member(const float4 *btris, const float *q, const float *blo,
                                                  const float *bhi, uint32_t leaf, int i) {
   if (leaf != 0xffffffffu) {
-    const float4 *T = p.B.tris + 3 * (size_t)leaf;
+    const float4 *T = btris + 3 * (size_t)leaf;
     float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -500,6 +534,68 @@ __device__ __forceinline__ float2 project_member(const Params &p, const float *q
   return make_float2(__fsub_rd(__fsub_rd(mlo, rad), sl), __fadd_ru(__fadd_ru(mhi, rad), sl));
 }
 
+// Treelet staging (Sec. III-B clusters the hierarchy into treelets sized to a cache; here the
+// cache is shared memory).  Thread 0 copies the leading treelets of A and of B -- the top of
+// each hierarchy, which every traversal passes through -- with one 1-D TMA bulk copy each
+// (cp.async.bulk, no multicast), completing on an mbarrier; the other threads copy the
+// matching prefix of the treelet offset table.  The wait on the mbarrier is bounded: if it
+// runs out the block reports CBVH_ERR_TIMEOUT and reads every treelet from global memory.
+// Returns whether the staged copies may be used (uniform in the block).
+constexpr long long kStageSpin = 1ll << 24;
+__device__ bool stage_treelets(const Params &p, uint8_t *smem) {
+  const Layout &L = p.L;
+  const int nst = (L.st_bytes[0] > 0) + (L.st_bytes[1] > 0);
+  if (nst == 0) return false;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.o_bar);
+  const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_s), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](const BVd &X, int k) {
+    if (L.st_bytes[k] <= 0) return;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem + L.st_off[k]);
+    const uint8_t *src = X.blob + X.toff[0];
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"((uint32_t)L.st_bytes[k]), "r"(bar_s)
+                 : "memory");
+  };
+  auto offsets = [&](const BVd &X, int k) {
+    unsigned long long *to = reinterpret_cast<unsigned long long *>(smem + L.st_toff[k]);
+    for (int t = threadIdx.x; t <= L.st_cnt[k]; t += blockDim.x) to[t] = X.toff[t];
+  };
+  if (threadIdx.x == 0) {
+    const uint32_t total = (uint32_t)(L.st_bytes[0] + L.st_bytes[1]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(total) : "memory");
+    issue(p.A, 0);
+    issue(p.B, 1);
+  }
+  offsets(p.A, 0);
+  offsets(p.B, 1);
+  uint32_t done = 0;
+  for (long long i = 0; i < kStageSpin && !done; ++i)
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+        : "=r"(done)
+        : "r"(bar_s), "r"(0u)
+        : "memory");
+  const bool ok = __syncthreads_and(done) != 0;
+  if (!ok) {
+    if (threadIdx.x == 0) set_status(p.status, CBVH_ERR_TIMEOUT);
+    // the copies may still be in flight: give them a further bounded wait before the block
+    // goes on without them (their shared memory is never read)
+    for (long long i = 0; i < kStageSpin && !done; ++i)
+      asm volatile(
+          "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+          : "=r"(done)
+          : "r"(bar_s), "r"(0u)
+          : "memory");
+  }
+  return ok;
+}
+
 // One round of the traversal.  Tasks are node pairs of one pose still to be expanded: in
 // round 0 the root pair of every pose, afterwards the pairs that earlier rounds handed on.
 // A warp runs Algorithm 1 depth-first from its task with an explicit stack; in a round that
@@ -507,20 +603,35 @@ __device__ __forceinline__ float2 project_member(const Params &p, const float *q
 // the next round's task buffer, so that the node-pair tree of a heavy pose is spread over
 // many warps.  The last round has no budget and finishes every task; when a task buffer is
 // full, warps simply keep their work.
-template <int MODE, int KA>
+template <int MODE, int KA, bool BATCH>
 __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(const Params p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t *smem = g_dsmem;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  uint8_t *ws = smem + wib * p.L.warp_bytes;
+  const bool staged = BATCH ? false : stage_treelets(p, smem);
+  uint8_t *ws = smem + p.L.cta_bytes + wib * p.L.warp_bytes;
   uint2 *stack = p.stacks + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * (size_t)p.L.stack_cap;
   uint2 *leafq = reinterpret_cast<uint2 *>(ws + p.L.o_leafq);
   float *pc = reinterpret_cast<float *>(ws + p.L.o_pose);
   constexpr int KS = (KA & 1) ? KA : KA + 1;
-  Side SA{reinterpret_cast<uint32_t *>(ws + p.L.o_tagA), reinterpret_cast<int2 *>(ws + p.L.o_latA),
-          reinterpret_cast<int *>(ws + p.L.o_pathA), KA, 0xffffffffu, nullptr};
-  Side SB{reinterpret_cast<uint32_t *>(ws + p.L.o_tagB), reinterpret_cast<int2 *>(ws + p.L.o_latB),
-          reinterpret_cast<int *>(ws + p.L.o_pathB), 3, 0xffffffffu, nullptr};
+  Side SA{reinterpret_cast<uint32_t *>(ws + p.L.o_tagA),
+          reinterpret_cast<int2 *>(ws + p.L.o_latA),
+          reinterpret_cast<int *>(ws + p.L.o_pathA),
+          KA,
+          0xffffffffu,
+          nullptr,
+          staged ? (uint32_t)p.L.st_cnt[0] : 0u,
+          p.L.st_off[0],
+          p.L.st_toff[0]};
+  Side SB{reinterpret_cast<uint32_t *>(ws + p.L.o_tagB),
+          reinterpret_cast<int2 *>(ws + p.L.o_latB),
+          reinterpret_cast<int *>(ws + p.L.o_pathB),
+          3,
+          0xffffffffu,
+          nullptr,
+          staged ? (uint32_t)p.L.st_cnt[1] : 0u,
+          p.L.st_off[1],
+          p.L.st_toff[1]};
   float *alo = reinterpret_cast<float *>(ws + p.L.o_aset);
   float *ahi = alo + kMaxM * KS;
   uint32_t *aref = reinterpret_cast<uint32_t *>(ahi + kMaxM * KS);
@@ -531,10 +642,20 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
   float *phi = plo + kMaxM * KS;
   uint32_t *bref = reinterpret_cast<uint32_t *>(phi + kMaxM * KS);
   uint32_t *bleaf = bref + kMaxM;
-  for (int i = lane; i <= p.A.tdepth; i += 32) SA.tag[i] = 0xffffffffu;
-  for (int i = lane; i <= p.B.tdepth; i += 32) SB.tag[i] = 0xffffffffu;
+  for (int i = lane; i <= p.L.tdA; i += 32) SA.tag[i] = 0xffffffffu;
+  for (int i = lane; i <= p.L.tdB; i += 32) SB.tag[i] = 0xffffffffu;
   __syncwarp();
-  const bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
+  // the query being served: fixed for a single query (read from the launch parameters), per
+  // work item for a batch (the item's hierarchy views are kept in the warp's shared memory)
+  BVd *bv = reinterpret_cast<BVd *>(ws + p.L.o_bvd);
+  const BVd &A = BATCH ? bv[0] : p.A;
+  const BVd &B = BATCH ? bv[1] : p.B;
+  const float *poses = p.poses;
+  uint8_t *hitp = p.hit;
+  float *distp = p.dist;
+  bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
+  int item = -1;
+  unsigned long long item_lo = 0;
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t n_in = p.round == 0 ? (uint32_t)p.n : min(*p.count_in, p.task_cap);
   const bool may_spill = !p.last_round;
@@ -548,25 +669,58 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
     if (lane == 0) task = atomicAdd(p.task_next, 1u);
     task = __shfl_sync(kFull, task, 0);
     if (task >= n_in) break;
-    uint32_t pose, a, b;
+    uint32_t gid, a, b;  // global pose id (equal to the pose index of a single query)
     bool root;
     if (p.round == 0) {
-      pose = task;
+      gid = task;
       a = b = 0;
       root = true;
     } else {
       const uint4 t = p.tasks_in[task];
-      pose = t.x;
+      gid = t.x;
       a = t.y;
       b = t.z;
       root = false;
     }
-    if ((int64_t)pose != cur_pose) {
+    if (BATCH) {
+      // find the work item holding this global pose id (uniform across the warp)
+      int lo = 0, hi = p.n_items - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.item_base[mid] <= gid)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      if (lo != item) {
+        item = lo;
+        const BatchItem &it = p.items[lo];
+        {
+          const uint32_t *src = reinterpret_cast<const uint32_t *>(&it.A);  // A and B are adjacent
+          uint32_t *dst = reinterpret_cast<uint32_t *>(bv);
+          for (int w = lane; w < (int)(2 * sizeof(BVd) / 4); w += 32) dst[w] = src[w];
+        }
+        poses = it.poses;
+        hitp = it.hit;
+        distp = it.dist;
+        early = (it.flags & CBVH_EARLY_EXIT) != 0;
+        item_lo = p.item_base[lo];
+        // node references and projections belong to the previous pair of hierarchies
+        for (int i = lane; i <= p.L.tdA; i += 32) SA.tag[i] = 0xffffffffu;
+        for (int i = lane; i <= p.L.tdB; i += 32) SB.tag[i] = 0xffffffffu;
+        SA.cur_t = SB.cur_t = 0xffffffffu;
+        keyA = keyB = 0xffffffffu;
+        cur_pose = -1;
+        __syncwarp();
+      }
+    }
+    const uint32_t pose = (uint32_t)(gid - item_lo);  // pose index within its query
+    if ((int64_t)gid != cur_pose) {
       keyB = 0xffffffffu;  // projections depend on the pose
       // ---- pose precompute: u_j = R^T d_j, |u_j|, [s_lo, s_hi] of d_j.t, and eta_j, a
       // bound on the rounding error of each component of u_j ----
-      cur_pose = pose;
-      if (lane < 12) pc[lane] = p.poses[12 * (size_t)pose + lane];
+      cur_pose = gid;
+      if (lane < 12) pc[lane] = poses[12 * (size_t)pose + lane];
       __syncwarp();
       if (lane < KA) {
         const int d0 = c_dir[lane][0], d1 = c_dir[lane][1], d2 = c_dir[lane][2];
@@ -589,25 +743,25 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
     // per-pose state: the root task initialises it; later tasks update it atomically
     float best = INFINITY;
     if (root) {
-      if (MODE == MODE_PQ && p.skip && p.skip[pose]) {  // intersecting: the distance is 0
-        if (lane == 0) p.dist[pose] = 0.f;
+      if (MODE == MODE_PQ && p.skip && p.skip[gid]) {  // intersecting: the distance is 0
+        if (lane == 0) distp[pose] = 0.f;
         continue;
       }
       if (lane == 0) {
         if (MODE == MODE_CD) {
-          p.hit[pose] = 0;
+          hitp[pose] = 0;
           if (p.counts) p.counts[pose] = 0;
         } else {
-          p.dist[pose] = INFINITY;
+          distp[pose] = INFINITY;
         }
       }
     } else if (MODE == MODE_PQ) {
       float v = 0.f;
-      if (lane == 0) v = *reinterpret_cast<volatile float *>(&p.dist[pose]);
+      if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
       best = __shfl_sync(kFull, v, 0);
     } else if (early) {
       int h = 0;
-      if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&p.hit[pose]);
+      if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
       if (__shfl_sync(kFull, h, 0)) continue;
     }
     float published = best;
@@ -626,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
       if (lane < cnt) {
         const uint2 e = leafq[nleaf + lane];
         V3 P[3], Q[3];
-        load_pair(p, pc, e.x, e.y, P, Q, ia, ib);
+        load_pair(A.tris, B.tris, pc, e.x, e.y, P, Q, ia, ib);
         if (MODE == MODE_CD)
           h = tri_hit(P, Q);
         else
@@ -657,7 +811,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
         for (int o = 16; o > 0; o >>= 1) dl = fminf(dl, __shfl_xor_sync(kFull, dl, o));
         best = fminf(best, dl);
         if (best < published) {
-          if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&p.dist[pose]), __float_as_uint(best));
+          if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&distp[pose]), __float_as_uint(best));
           published = best;
         }
         if (best == 0.f) done = true;
@@ -670,17 +824,17 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
       // order one of them is often the same as in the previous expansion and is reused.
       int na, nb;
       if (a != keyA || root) {
-        na = decode_set(p.A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
+        na = decode_set(A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
         keyA = root ? 0xffffffffu : a;
         na_c = na;
       } else {
         na = na_c;
       }
       if (b != keyB || root) {
-        nb = decode_set(p.B, SB, b, root, lane, blo, bhi, 4, bref, bleaf, false);
+        nb = decode_set(B, SB, b, root, lane, blo, bhi, 4, bref, bleaf, false);
         for (int it = lane; it < nb * KA; it += 32) {
           const int i = it / KA, j = it - i * KA;
-          const float2 r = project_member(p, pose_dir(pc, j), blo, bhi, bleaf[i], i);
+          const float2 r = project_member(B.tris, pose_dir(pc, j), blo, bhi, bleaf[i], i);
           plo[i * KS + j] = r.x;
           phi[i * KS + j] = r.y;
         }
@@ -789,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
         if (ok) {
           for (int k = lane; k < sp; k += 32) {
             const uint2 e = stack[k];
-            p.tasks_out[base + k] = make_uint4(pose, e.x, e.y, 0u);
+            p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, 0u);
           }
           sp = 0;
           __syncwarp();
@@ -799,11 +953,11 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
       if ((expansions & 15) == 0) {
         if (MODE == MODE_PQ) {
           float v = 0.f;
-          if (lane == 0) v = *reinterpret_cast<volatile float *>(&p.dist[pose]);
+          if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
           best = fminf(best, __shfl_sync(kFull, v, 0));
         } else if (early) {
           int h = 0;
-          if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&p.hit[pose]);
+          if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
           if (__shfl_sync(kFull, h, 0)) break;
         }
       }
@@ -818,11 +972,11 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
     if (lane == 0) {
       if (MODE == MODE_CD) {
         if (nhits) {
-          p.hit[pose] = 1;
+          hitp[pose] = 1;
           if (p.counts) atomicAdd(&p.counts[pose], nhits);
         }
       } else if (best < published) {
-        atomicMin(reinterpret_cast<unsigned int *>(&p.dist[pose]), __float_as_uint(best));
+        atomicMin(reinterpret_cast<unsigned int *>(&distp[pose]), __float_as_uint(best));
       }
     }
     __syncwarp();
@@ -1008,12 +1162,18 @@ BVd view(const cbvh_bvh *h) {
 
 int align16(int x) { return (x + 15) & ~15; }
 
-Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
+// Process-wide tuning options (cbvh_set_option).
+std::atomic<int> g_stage_bytes{kStageBytesDefault};
+
+// Per-warp slice layout for A's direction count, the deepest nodes below a treelet root on
+// either side and a stack bound; no staged treelets.
+Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   Layout L;
-  const int KA = A->K;
+  std::memset(&L, 0, sizeof L);
+  L.tdA = tdA;
+  L.tdB = tdB;
   L.KS = (KA & 1) ? KA : KA + 1;
-  // stack bound: every level of the node-pair tree leaves at most (mA mB - 1) siblings
-  L.stack_cap = 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1);
+  L.stack_cap = stack_cap;
   L.leafq_cap = 64;  // < 32 queued before a round of tests, a round adds <= 32
   int o = 0;
   L.o_stack = -1;  // stacks live in global memory
@@ -1022,22 +1182,57 @@ Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
   L.o_pose = o;
   o = align16(o + 4 * (12 + kPoseJ * KA));
   L.o_tagA = o;
-  o = align16(o + 4 * (A->max_tdepth + 1));
+  o = align16(o + 4 * (tdA + 1));
   L.o_latA = o;
-  o = align16(o + 8 * (A->max_tdepth + 1) * KA);
+  o = align16(o + 8 * (tdA + 1) * KA);
   L.o_pathA = o;
-  o = align16(o + 4 * (A->max_tdepth + 1));
+  o = align16(o + 4 * (tdA + 1));
   L.o_tagB = o;
-  o = align16(o + 4 * (B->max_tdepth + 1));
+  o = align16(o + 4 * (tdB + 1));
   L.o_latB = o;
-  o = align16(o + 8 * (B->max_tdepth + 1) * 3);
+  o = align16(o + 8 * (tdB + 1) * 3);
   L.o_pathB = o;
-  o = align16(o + 4 * (B->max_tdepth + 1));
+  o = align16(o + 4 * (tdB + 1));
   L.o_aset = o;
   o = align16(o + 4 * (2 * kMaxM * L.KS + 2 * kMaxM));
   L.o_bset = o;
   o = align16(o + 4 * (2 * kMaxM * 4 + 2 * kMaxM * L.KS + 2 * kMaxM));
+  L.o_bvd = o;
+  o = align16(o + 2 * (int)sizeof(BVd));
   L.warp_bytes = o;
+  return L;
+}
+
+// Stack bound: every level of the node-pair tree leaves at most (mA mB - 1) siblings.
+int stack_bound(const cbvh_bvh *A, const cbvh_bvh *B) { return 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1); }
+
+Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
+  Layout L = warp_layout(A->K, A->max_tdepth, B->max_tdepth, stack_bound(A, B));
+  // CTA region: the leading treelets of A and B that fit the staging budget
+  int o = 0;
+  const cbvh_bvh *H[2] = {A, B};
+  const int budget = g_stage_bytes.load();
+  for (int k = 0; k < 2; ++k) {
+    const uint8_t *b = H[k]->blob.data();
+    auto toff = [&](int64_t t) {
+      uint64_t v;
+      std::memcpy(&v, b + 64 + 8 * t, 8);
+      return (int64_t)v;
+    };
+    int cnt = 0;
+    while (cnt < H[k]->n_treelets && toff(cnt + 1) - toff(0) <= budget) ++cnt;
+    L.st_cnt[k] = cnt;
+    L.st_bytes[k] = (int)(toff(cnt) - toff(0));
+    L.st_off[k] = o;
+    o += (L.st_bytes[k] + 127) & ~127;
+  }
+  for (int k = 0; k < 2; ++k) {
+    L.st_toff[k] = o;
+    o = align16(o + 8 * (L.st_cnt[k] + 1));
+  }
+  L.o_bar = o;
+  o = align16(o + 8);
+  L.cta_bytes = (o + 127) & ~127;
   return L;
 }
 
@@ -1062,9 +1257,9 @@ constexpr int kRounds = 6;
 constexpr int kBudget[kRounds] = {16, 32, 64, 128, 512, 0};
 constexpr int kMaxWarpsPerSM = 64;
 
-// Workspace layout: [0, 256) counters -- u64 pair count at 0, u64 stats[3] at 16, u32 task
-// cursor per round at 64, u32 task count per round at 128 (one block of cursors and counts
-// per pass) -- then the per-pose pair counts and (pose, i, j) triples (collide with pairs),
+// Workspace layout: [0, 256) counters -- u64 pair count at 0, u64 stats[3] at 16, then per
+// pass 64 bytes of round counters (task cursor and task count of each round) at 64 and
+// 128 -- then the per-pose pair counts and (pose, i, j) triples (collide with pairs),
 // per-pose intersection flags (distance), two task buffers and the per-warp stacks.
 constexpr int64_t kWsHeader = 256;
 struct WsPlan {
@@ -1104,20 +1299,27 @@ int device_sms(int *sms) {
 
 // The traversal kernel compiled for A's number of slab directions (k = 6, 18, 24, 26).
 typedef void (*TraverseFn)(const Params);
-template <int MODE>
-TraverseFn traverse_fn(int K) {
+template <int MODE, bool BATCH>
+TraverseFn traverse_fn_b(int K) {
   switch (K) {
-    case 3: return traverse_kernel<MODE, 3>;
-    case 9: return traverse_kernel<MODE, 9>;
-    case 12: return traverse_kernel<MODE, 12>;
-    default: return traverse_kernel<MODE, 13>;
+    case 3: return traverse_kernel<MODE, 3, BATCH>;
+    case 9: return traverse_kernel<MODE, 9, BATCH>;
+    case 12: return traverse_kernel<MODE, 12, BATCH>;
+    default: return traverse_kernel<MODE, 13, BATCH>;
   }
 }
-
 template <int MODE>
-int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t s, int pass = 0, int slot = MODE) {
-  const int smem = kWarpsPerBlock * p.L.warp_bytes;
-  const TraverseFn fn = traverse_fn<MODE>(p.A.K);
+TraverseFn traverse_fn(int K, bool batch = false) {
+  return batch ? traverse_fn_b<MODE, true>(K) : traverse_fn_b<MODE, false>(K);
+}
+
+// Launches the rounds of one traversal pass.  ctr: 16 zeroed u32 counters (task cursor and
+// task count of every round); buf: the two task buffers; stacks: per-warp stacks.
+template <int MODE>
+int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint2 *stacks, uint32_t task_cap, int sms,
+                  cudaStream_t s, int slot = MODE) {
+  const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
+  const TraverseFn fn = traverse_fn<MODE>(p.A.K, p.items != nullptr);
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
@@ -1126,11 +1328,9 @@ int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t
   if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
   per_sm = std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock);
   const int blocks = sms * per_sm;
-  unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64) + 8 * pass;
-  unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128) + 8 * pass;
-  uint4 *buf[2] = {reinterpret_cast<uint4 *>(ws + w.tasks0), reinterpret_cast<uint4 *>(ws + w.tasks1)};
-  p.stacks = reinterpret_cast<uint2 *>(ws + w.stacks);
-  p.task_cap = w.task_cap;
+  uint4 *buf[2] = {buf0, buf1};
+  p.stacks = stacks;
+  p.task_cap = task_cap;
   ProfRec rec{nullptr, nullptr, slot};
   if (g_prof.on) {
     if (!g_prof.spare.empty()) {
@@ -1146,9 +1346,9 @@ int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t
     p.round = r;
     p.last_round = r == kRounds - 1;
     p.budget = kBudget[r];
-    p.task_next = next + r;
-    p.count_in = count + r;
-    p.count_out = count + r + 1;
+    p.task_next = ctr + r;
+    p.count_in = ctr + 8 + r;
+    p.count_out = ctr + 8 + r + 1;
     p.tasks_in = buf[(r + 1) & 1];
     p.tasks_out = buf[r & 1];
     fn<<<blocks, kThreads, smem, s>>>(p);
@@ -1160,6 +1360,14 @@ int launch_rounds(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t
   }
   if (e != cudaSuccess) return cuda_fail(e, "traverse launch");
   return CBVH_OK;
+}
+
+// Single query: counters of pass k at ws + 64 (k + 1), buffers and stacks from the plan.
+template <int MODE>
+int launch_single(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t s, int pass = 0, int slot = MODE) {
+  return launch_rounds<MODE>(p, reinterpret_cast<unsigned int *>(ws + 64 * (pass + 1)),
+                             reinterpret_cast<uint4 *>(ws + w.tasks0), reinterpret_cast<uint4 *>(ws + w.tasks1),
+                             reinterpret_cast<uint2 *>(ws + w.stacks), w.task_cap, sms, s, slot);
 }
 
 int check_pair(const cbvh_bvh *A, const cbvh_bvh *B) {
@@ -1264,7 +1472,7 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
     p.triples = triples;
     p.cap = (unsigned long long)pair_capacity;
   }
-  if (int rc = launch_rounds<MODE_CD>(p, ws, w, sms, s)) return rc;
+  if (int rc = launch_single<MODE_CD>(p, ws, w, sms, s)) return rc;
   if (want_pairs) {
     ProfRec rec{nullptr, nullptr, 2};
     if (g_prof.on) {
@@ -1322,14 +1530,14 @@ extern "C" int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *
   q.status = status;
   q.pair_count = reinterpret_cast<unsigned long long *>(ws);
   q.stats = reinterpret_cast<unsigned long long *>(ws + 16);
-  if (int rc = launch_rounds<MODE_CD>(q, ws, w, sms, s, 0, 1)) return rc;
+  if (int rc = launch_single<MODE_CD>(q, ws, w, sms, s, 0, 1)) return rc;
   p.poses = poses;
   p.n = n;
   p.dist = dist;
   p.status = status;
   p.skip = ws + w.flags;
   p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
-  return launch_rounds<MODE_PQ>(p, ws, w, sms, s, 1);
+  return launch_single<MODE_PQ>(p, ws, w, sms, s, 1);
 }
 
 extern "C" int cbvh_query_stats(const void *workspace, int64_t *stats_host, void *stream) {
@@ -1418,8 +1626,8 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
     return cbvh::fail(CBVH_ERR_WORKSPACE,
                       "this pair of hierarchies needs " + std::to_string(per_warp * kWarpsPerBlock + stacks_off) +
                           " bytes of scratch; cbvh_distance_noalloc has " + std::to_string(kNoAllocScratchBytes));
-  const int smem = kWarpsPerBlock * p.L.warp_bytes;
-  const TraverseFn fn = traverse_fn<MODE_PQ>(p.A.K);
+  const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
+  const TraverseFn fn = traverse_fn<MODE_PQ>(p.A.K, false);
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
@@ -1458,4 +1666,221 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "traverse launch");
+}
+
+// ---------------------------------------------------------------- batched queries
+// A batch is a list of work items (A, B, kind, poses, outputs).  Items are grouped by kind and
+// by A's direction count; each group runs as one pass of persistent rounds over all of its
+// poses (two passes for distances: the early-exit collision pass, then branch and bound), so
+// pairs of hierarchies of different sizes share the GPU and a heavy item spreads over all
+// warps.  Upload writes the item table into the workspace; launch only enqueues kernels and
+// memsets, so it can be captured in a CUDA graph and replayed.
+struct cbvh_batch {
+  struct Group {
+    int mode, first, count, pre_first;
+    int64_t poses, bases_at, skip_off;
+    Layout L;
+    BVd A0, B0;
+  };
+  std::vector<BatchItem> items;
+  std::vector<unsigned long long> bases;
+  std::vector<Group> groups;
+  int64_t o_ctr = 0, o_items = 0, o_bases = 0, o_tasks0 = 0, o_tasks1 = 0, o_stacks = 0, total = 0;
+  uint32_t task_cap = 0;
+  int sms = 0;
+};
+
+extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch **out) {
+  cbvh::clear_error();
+  if (!out || (nq > 0 && !q) || nq < 0) return cbvh::fail(CBVH_ERR_ARG, "bad argument");
+  *out = nullptr;
+  for (int64_t i = 0; i < nq; ++i) {
+    const cbvh_query_t &x = q[i];
+    if (int rc = check_pair(x.A, x.B)) return rc;
+    if ((x.mode != 0 && x.mode != 1) || x.n < 0 || (x.n > 0 && !x.poses))
+      return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": bad mode, size or poses");
+    if (x.n > 0 && ((x.mode == 0 && !x.hit) || (x.mode == 1 && !x.dist)))
+      return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": missing output");
+    if (x.mode == 1 && x.flags) return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": flags are for collision");
+    if (x.flags & ~CBVH_EARLY_EXIT) return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": unknown flags");
+  }
+  auto b = new cbvh_batch();
+  if (int rc = device_sms(&b->sms)) {
+    delete b;
+    return rc;
+  }
+  int64_t total_poses = 0, max_group = 0;
+  int max_stack = 1;
+  for (int mode = 0; mode < 2; ++mode)
+    for (int K : {3, 9, 12, 13}) {
+      std::vector<int64_t> idx;
+      for (int64_t i = 0; i < nq; ++i)
+        if (q[i].mode == mode && q[i].A->K == K) idx.push_back(i);
+      if (idx.empty()) continue;
+      cbvh_batch::Group g;
+      g.mode = mode;
+      g.first = (int)b->items.size();
+      g.count = (int)idx.size();
+      g.bases_at = (int64_t)b->bases.size();
+      int tdA = 0, tdB = 0, sc = 1;
+      unsigned long long acc = 0;
+      for (int64_t i : idx) {
+        const cbvh_query_t &x = q[i];
+        BatchItem it;
+        std::memset(&it, 0, sizeof it);
+        it.A = view(x.A);
+        it.B = view(x.B);
+        it.poses = x.poses;
+        it.hit = x.hit;
+        it.dist = x.dist;
+        it.flags = x.flags;
+        b->items.push_back(it);
+        b->bases.push_back(acc);
+        acc += (unsigned long long)x.n;
+        tdA = std::max(tdA, x.A->max_tdepth);
+        tdB = std::max(tdB, x.B->max_tdepth);
+        sc = std::max(sc, stack_bound(x.A, x.B));
+      }
+      b->bases.push_back(acc);
+      g.poses = (int64_t)acc;
+      g.L = warp_layout(K, tdA, tdB, sc);
+      g.A0 = view(q[idx[0]].A);
+      g.B0 = view(q[idx[0]].B);
+      g.pre_first = -1;
+      g.skip_off = -1;
+      max_stack = std::max(max_stack, sc);
+      max_group = std::max(max_group, g.poses);
+      total_poses += g.poses;
+      b->groups.push_back(g);
+    }
+  // distance groups also get a collision item table for their early-exit pass
+  for (auto &g : b->groups) {
+    if (g.mode != 1) continue;
+    g.pre_first = (int)b->items.size();
+    for (int k = 0; k < g.count; ++k) {
+      BatchItem it = b->items[g.first + k];
+      it.dist = nullptr;
+      it.hit = nullptr;  // set at upload: the group's intersection flags + item base
+      it.flags = CBVH_EARLY_EXIT;
+      b->items.push_back(it);
+    }
+  }
+  // workspace plan
+  int64_t o = kWsHeader;
+  b->o_ctr = o;
+  o = align256(o + 128 * (int64_t)b->groups.size());
+  b->o_items = o;
+  o = align256(o + (int64_t)sizeof(BatchItem) * (int64_t)b->items.size());
+  b->o_bases = o;
+  o = align256(o + 8 * (int64_t)b->bases.size());
+  for (auto &g : b->groups)
+    if (g.mode == 1) {
+      g.skip_off = o;
+      o = align256(o + g.poses);
+    }
+  const int64_t tcap = std::min<int64_t>(std::max<int64_t>(int64_t(1) << 20, 256 * max_group), int64_t(1) << 30);
+  b->task_cap = (uint32_t)tcap;
+  b->o_tasks0 = o;
+  o = align256(o + 16 * tcap);
+  b->o_tasks1 = o;
+  o = align256(o + 16 * tcap);
+  b->o_stacks = o;
+  o = align256(o + (int64_t)b->sms * kMaxWarpsPerSM * max_stack * 8);
+  b->total = o;
+  (void)total_poses;
+  *out = b;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_batch_free(cbvh_batch *b) {
+  delete b;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_batch_workspace_bytes(const cbvh_batch *b, int64_t *bytes) {
+  cbvh::clear_error();
+  if (!b || !bytes) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  *bytes = b->total;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_batch_upload(const cbvh_batch *b, void *workspace, int64_t workspace_bytes, void *stream) {
+  cbvh::clear_error();
+  if (!b) return cbvh::fail(CBVH_ERR_ARG, "NULL batch");
+  if (!workspace || workspace_bytes < b->total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  std::vector<BatchItem> items = b->items;
+  for (const auto &g : b->groups)
+    if (g.mode == 1)
+      for (int k = 0; k < g.count; ++k)
+        items[g.pre_first + k].hit = ws + g.skip_off + b->bases[g.bases_at + k];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(ws + b->o_items, items.data(), sizeof(BatchItem) * items.size(),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + b->o_bases, b->bases.data(), 8 * b->bases.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "cbvh_batch_upload");
+}
+
+extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_bytes, int32_t *status,
+                                 void *stream) {
+  cbvh::clear_error();
+  if (!b || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  if (!workspace || workspace_bytes < b->total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(ws, 0, b->o_items, s);  // header and round counters
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const BatchItem *dev_items = reinterpret_cast<const BatchItem *>(ws + b->o_items);
+  const unsigned long long *dev_bases = reinterpret_cast<const unsigned long long *>(ws + b->o_bases);
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const auto &g = b->groups[gi];
+    if (g.poses == 0) continue;
+    Params p;
+    std::memset(&p, 0, sizeof p);
+    p.A = g.A0;
+    p.B = g.B0;
+    p.L = g.L;
+    for (int j = 0; j < kMaxK; ++j) {
+      static const int n2[kMaxK] = {1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3};
+      float f = (float)(1.0 / std::sqrt((double)n2[j]));
+      while ((double)f * (double)f * n2[j] > 1.0) f = std::nextafter(f, 0.0f);
+      p.invn[j] = f;
+    }
+    p.item_base = dev_bases + g.bases_at;
+    p.n_items = g.count;
+    p.n = g.poses;
+    p.status = status;
+    p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+    p.pair_count = reinterpret_cast<unsigned long long *>(ws);
+    unsigned int *ctr = reinterpret_cast<unsigned int *>(ws + b->o_ctr + 128 * (int64_t)gi);
+    uint4 *t0 = reinterpret_cast<uint4 *>(ws + b->o_tasks0), *t1 = reinterpret_cast<uint4 *>(ws + b->o_tasks1);
+    uint2 *st = reinterpret_cast<uint2 *>(ws + b->o_stacks);
+    if (g.mode == 0) {
+      p.items = dev_items + g.first;
+      if (int rc = launch_rounds<MODE_CD>(p, ctr, t0, t1, st, b->task_cap, b->sms, s)) return rc;
+    } else {
+      Params c = p;
+      c.items = dev_items + g.pre_first;
+      if (int rc = launch_rounds<MODE_CD>(c, ctr, t0, t1, st, b->task_cap, b->sms, s, 1)) return rc;
+      p.items = dev_items + g.first;
+      p.skip = ws + g.skip_off;
+      if (int rc = launch_rounds<MODE_PQ>(p, ctr + 16, t0, t1, st, b->task_cap, b->sms, s)) return rc;
+    }
+  }
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_set_option(int option, int64_t value) {
+  cbvh::clear_error();
+  if (option == CBVH_OPT_STAGE_BYTES) {
+    if (value < 0 || value > 32768) return cbvh::fail(CBVH_ERR_ARG, "stage bytes must be in [0, 32768]");
+    g_stage_bytes.store((int)value);
+    return CBVH_OK;
+  }
+  return cbvh::fail(CBVH_ERR_ARG, "unknown option");
 }

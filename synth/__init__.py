@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "icosphere", "heightfield", "ValueNoise2D", "box_mesh", "capsule", "shoemake_rotations",
     "poses_box", "poses_terrain", "dh_link_poses", "merge_meshes", "transform_mesh",
-    "scene_diameter", "C1", "C2",
+    "scene_diameter", "C1", "C2", "C3", "clutter", "arm_links",
 ]
 
 _PHI = (1.0 + math.sqrt(5.0)) / 2.0
@@ -339,3 +339,47 @@ def C2(n_poses: int = 10000, cells: int = 512):
     B = icosphere(5, 1.0, 0.15, seed=1012)
     P = poses_terrain(n_poses, seed=2002, height_fn=H)
     return dict(A=(va, ta), B=B, poses=P, k=24, m=8, bits=8, treelet=16384, height=H)
+
+
+def clutter(n_boxes: int = 200, n_spheres: int = 200, seed: int = 1003, level: int = 4, half: float = 2.0):
+    """Static clutter scene: boxes (side U(0.05, 0.4)) and displaced level-`level` spheres
+    (radius U(0.05, 0.3)), placed uniformly in [-half, half]^3 with uniform rotations."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k in range(n_boxes):
+        v, t = box_mesh(rng.uniform(0.05, 0.4, size=3))
+        R = shoemake_rotations(rng, 1)[0]
+        parts.append((transform_mesh(v, R, rng.uniform(-half, half, size=3)), t))
+    for k in range(n_spheres):
+        v, t = icosphere(level, rng.uniform(0.05, 0.3), 0.15, seed=seed * 7 + k)
+        R = shoemake_rotations(rng, 1)[0]
+        parts.append((transform_mesh(v, R, rng.uniform(-half, half, size=3)), t))
+    return merge_meshes(parts)
+
+
+def arm_links(a: float = 0.3, seed: int = 1013, sizes=(5120, 10000, 20480, 40000, 10000, 5120)):
+    """The six link meshes of a serial arm, each in its own DH link frame, spanning x in
+    [-a, 0] (from the previous joint to the frame origin): level-4 and level-5 displaced
+    icospheres for the 5,120 and 20,480 sizes, displaced capsules for the others."""
+    links = []
+    for i, n in enumerate(sizes):
+        if n in (5120, 20480):
+            v, t = icosphere(4 if n == 5120 else 5, a / 2, 0.1, seed=seed + i)
+            v = v + np.array([-a / 2, 0, 0], np.float32)
+        else:
+            v, t = capsule(a * 0.8, 0.05, n, disp=0.05, seed=seed + i)
+            v = v + np.array([-a * 0.9, 0, 0], np.float32)
+        links.append((v.astype(np.float32), t))
+    return links
+
+
+def C3(n_configs: int = 200000, n_boxes: int = 200, n_spheres: int = 200):
+    """Motion-planning sweep: a 6-link DH arm (a = 0.3, alternating alpha = +-pi/2) against a
+    static clutter scene of boxes and spheres in a 4 m cube; joint angles U[-pi, pi]^6.
+    Returns the clutter (A), the links (B_i) and per-link poses (n, 6, 12).  Seeds 1003,
+    1013 (meshes), 2003 (configurations)."""
+    A = clutter(n_boxes, n_spheres)
+    links = arm_links()
+    rng = np.random.default_rng(2003)
+    q = rng.uniform(-np.pi, np.pi, size=(n_configs, 6))
+    return dict(A=A, links=links, link_poses=dh_link_poses(q), q=q, k=24, m=8, bits=8, treelet=16384)

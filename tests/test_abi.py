@@ -106,3 +106,15 @@ def test_queries_without_device_blob_are_rejected(cb):
     else:
         assert cb.lib.cbvh_last_error()
     assert cb.lib.cbvh_workspace_bytes(A.handle, B.handle, -1, 0, 0, C.byref(out)) == -1
+
+
+def test_batch_rejects_unattached_handles(cb):
+    v, t = synth.icosphere(1, seed=1)
+    A = cb.BVH(v, t, device=None)
+    B = cb.BVH(v, t, device=None)
+    q = (cb._Query * 1)()
+    q[0] = cb._Query(A.handle, B.handle, 0, 0, None, 0, None, None)
+    h = C.c_void_p()
+    assert cb.lib.cbvh_batch_create(q, 1, C.byref(h)) == -9
+    assert cb.lib.cbvh_set_option(99, 0) == -1
+    assert cb.lib.cbvh_set_option(cb.OPT_STAGE_BYTES, 1 << 20) == -1

@@ -1,0 +1,123 @@
+"""Batched queries (cbvh_batch_*) on the GPU.
+
+- Every item of a mixed batch (different pairs of hierarchies, collision with and without
+  early exit, distances) returns exactly what the same query returns on its own.
+- The batch launch can be captured in a CUDA graph; replays reproduce the direct results.
+- A reduced arm-against-clutter sweep agrees with the FP64 oracle on poses away from contact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_05348_gb300 import _build
+    _build.build()
+    import paper_2012_05348_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def scene(cb):
+    import torch
+    c1 = synth.C1(300)
+    (va, ta), (vb, tb) = c1["A"], c1["B"]
+    S1 = cb.BVH(va, ta, 18, 4, 16, 4096)
+    S2 = cb.BVH(vb, tb, 18, 4, 16, 4096)
+    S3 = cb.BVH(vb, tb, 18, 8, 8, 16384)   # a second B, different branching
+    c3 = synth.C3(400, n_boxes=30, n_spheres=30)
+    clutter = cb.BVH(*c3["A"], 24, 8, 8, 16384)
+    links = [cb.BVH(*l, 24, 8, 8, 16384) for l in c3["links"]]
+    P1 = torch.as_tensor(c1["poses"], device="cuda")
+    LP = [torch.as_tensor(np.ascontiguousarray(c3["link_poses"][:, i]), device="cuda") for i in range(6)]
+    return dict(S1=S1, S2=S2, S3=S3, P1=P1, clutter=clutter, links=links, LP=LP, c3=c3, c1=c1)
+
+
+def _items(sc):
+    it = [dict(A=sc["S1"], B=sc["S2"], kind="collide", poses=sc["P1"]),
+          dict(A=sc["S1"], B=sc["S3"], kind="collide", poses=sc["P1"][:137], early_exit=True),
+          dict(A=sc["S1"], B=sc["S2"], kind="distance", poses=sc["P1"][:211]),
+          dict(A=sc["S1"], B=sc["S3"], kind="distance", poses=sc["P1"][50:90])]
+    for i, (L, P) in enumerate(zip(sc["links"], sc["LP"])):
+        it.append(dict(A=sc["clutter"], B=L, kind="collide", poses=P, early_exit=True))
+    it.append(dict(A=sc["clutter"], B=sc["links"][3], kind="distance", poses=sc["LP"][3][:100]))
+    return it
+
+
+def _alone(cb, it):
+    if it["kind"] == "collide":
+        return cb.collide(it["A"], it["B"], it["poses"], pairs=False, early_exit=bool(it.get("early_exit"))).hit
+    return cb.distance(it["A"], it["B"], it["poses"])
+
+
+def test_batch_items_equal_single_queries(cb, scene):
+    items = _items(scene)
+    batch = cb.Batch(items)
+    outs = batch.run()
+    for it, out in zip(items, outs):
+        ref = _alone(cb, it).cpu().numpy()
+        got = out.cpu().numpy()
+        if it["kind"] == "collide":
+            assert (got == ref).all()
+        else:
+            # the visiting order differs between the two launches, so a pruned pair whose FP32
+            # distance lies within rounding of its lower bound may change the last ulps
+            assert np.allclose(got, ref, rtol=0, atol=1e-5 * 8.0)
+    hits = np.stack([o.cpu().numpy() for o in outs[4:10]])
+    assert 0 < hits.any(0).sum() < hits.shape[1]  # some configurations collide, some do not
+
+
+def test_batch_graph_capture_and_replay(cb, scene):
+    import torch
+    items = _items(scene)
+    batch = cb.Batch(items)
+    direct = [o.clone() for o in batch.run()]
+    for o in batch.outputs:
+        o.fill_(77)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        batch.launch(stream)  # warm the launch path outside capture
+    torch.cuda.current_stream().wait_stream(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.launch()
+    for _ in range(2):
+        for o in batch.outputs:
+            o.fill_(77)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(batch.status.item()) == 0
+        for it, a, b in zip(items, direct, batch.outputs):
+            if it["kind"] == "collide":
+                assert torch.equal(a, b)
+            else:  # branch-and-bound visiting order may move the last ulps
+                assert torch.allclose(a, b, rtol=0, atol=1e-5 * 8.0)
+
+
+def test_arm_sweep_against_oracle(cb, scene):
+    c3 = scene["c3"]
+    A = oracle.BVH(*c3["A"], 24, 8, 8, 16384)
+    items = [dict(A=scene["clutter"], B=L, kind="collide", poses=P) for L, P in zip(scene["links"], scene["LP"])]
+    outs = [o.cpu().numpy() for o in cb.Batch(items).run()]
+    va = c3["A"][0]
+    checked = 0
+    for i, (v, t) in enumerate(c3["links"]):
+        B = oracle.BVH(v, t, 24, 8, 8, 16384)
+        P = c3["link_poses"][:60, i]
+        D = synth.scene_diameter(va, v)
+        near, _ = oracle.near_contact(A, B, P, 1e-6 * D)
+        hit, *_ = oracle.collide(A, B, P)
+        ok = ~near
+        assert (outs[i][:60][ok] == hit[ok]).all()
+        checked += int(ok.sum())
+    assert checked > 200
