@@ -182,6 +182,10 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
  *   copies into shared memory (TMA bulk copy) before a single query, 0..32768 (default
  *   16384; 0 disables).  Takes effect for queries issued afterwards. */
 #define CBVH_OPT_STAGE_BYTES 1
+/*   CBVH_OPT_SPLIT: work mapping.  1 (default): a pose's node-pair tree is split into tasks
+ *   that later rounds spread over all warps (warp per node pair); 0: one round in which
+ *   each warp traverses whole poses (warp per pose). */
+#define CBVH_OPT_SPLIT 2
 int cbvh_set_option(int option, int64_t value);
 
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests

@@ -1164,6 +1164,7 @@ int align16(int x) { return (x + 15) & ~15; }
 
 // Process-wide tuning options (cbvh_set_option).
 std::atomic<int> g_stage_bytes{kStageBytesDefault};
+std::atomic<int> g_split{1};  // 1: node-pair tasks handed on between rounds; 0: one warp per pose
 
 // Per-warp slice layout for A's direction count, the deepest nodes below a treelet root on
 // either side and a stack bound; no staged treelets.
@@ -1342,9 +1343,10 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint2 
     }
     cudaEventRecord(rec.a, s);
   }
-  for (int r = 0; r < kRounds; ++r) {
+  const int rounds = g_split.load() ? kRounds : 1;
+  for (int r = 0; r < rounds; ++r) {
     p.round = r;
-    p.last_round = r == kRounds - 1;
+    p.last_round = r == rounds - 1;
     p.budget = kBudget[r];
     p.task_next = ctr + r;
     p.count_in = ctr + 8 + r;
@@ -1880,6 +1882,11 @@ extern "C" int cbvh_set_option(int option, int64_t value) {
   if (option == CBVH_OPT_STAGE_BYTES) {
     if (value < 0 || value > 32768) return cbvh::fail(CBVH_ERR_ARG, "stage bytes must be in [0, 32768]");
     g_stage_bytes.store((int)value);
+    return CBVH_OK;
+  }
+  if (option == CBVH_OPT_SPLIT) {
+    if (value != 0 && value != 1) return cbvh::fail(CBVH_ERR_ARG, "split must be 0 or 1");
+    g_split.store((int)value);
     return CBVH_OK;
   }
   return cbvh::fail(CBVH_ERR_ARG, "unknown option");

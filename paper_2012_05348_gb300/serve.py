@@ -1,0 +1,205 @@
+"""Request loop with continuous batching for collision and distance queries.
+
+Planners submit requests -- (environment, robot, kind, poses) -- from any thread and get a
+future.  A serving thread keeps every hierarchy resident on the device and admits waiting
+requests into batches as stream slots and device memory free up: requests that arrive while
+others are on the GPU join the next batch, each batch runs as one set of persistent launches
+(cbvh_batch_launch) on its own stream, and up to ``slots`` batches overlap on the device.
+Admission is by a device-memory budget: a batch takes requests in arrival order while the
+memory it needs (poses, outputs, workspace) fits in what the budget has left.  Per-request
+latency (submit to result) is recorded for p50 / p99.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+
+import numpy as np
+
+from . import Batch, CbvhError, _torch
+
+
+class Request:
+    __slots__ = ("env", "robot", "kind", "poses", "early_exit", "future", "t_submit", "t_done")
+
+    def __init__(self, env, robot, kind, poses, early_exit):
+        self.env, self.robot, self.kind, self.poses, self.early_exit = env, robot, kind, poses, early_exit
+        self.future = Future()
+        self.t_submit = time.perf_counter()
+        self.t_done = None
+
+
+class Server:
+    """models: name -> attached BVH.  mem_budget: device bytes that batches in flight may use.
+    max_poses: cap on the poses of one batch."""
+
+    def __init__(self, models: dict, mem_budget: int = 1 << 30, slots: int = 2, max_poses: int = 1 << 16,
+                 device="cuda"):
+        torch = _torch()
+        self.models = models
+        self.mem_budget = int(mem_budget)
+        self.max_poses = int(max_poses)
+        dev = torch.device(device)
+        self.device = torch.device("cuda", dev.index if dev.index is not None else torch.cuda.current_device())
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.busy = [None] * slots  # per slot: (event, requests, host outputs, bytes)
+        self.used = 0
+        self.pending = collections.deque()
+        self.cv = threading.Condition()
+        self.latencies = []
+        self.batches = 0
+        self.running = True
+        self.error = None
+        self.thread = threading.Thread(target=self._loop, name="cbvh-serve", daemon=True)
+        self.thread.start()
+
+    # ---------------------------------------------------------------- client side
+    def submit(self, env: str, robot: str, kind: str, poses: np.ndarray, early_exit: bool = False) -> Future:
+        """Queue a request; the future resolves to uint8 hit flags ('collide') or float32
+        distances ('distance'), one per pose."""
+        if kind not in ("collide", "distance"):
+            raise ValueError("kind must be 'collide' or 'distance'")
+        if env not in self.models or robot not in self.models:
+            raise KeyError("unknown model")
+        poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 12)
+        r = Request(env, robot, kind, poses, early_exit)
+        with self.cv:
+            if not self.running:
+                raise RuntimeError("server is closed")
+            self.pending.append(r)
+            self.cv.notify()
+        return r.future
+
+    def close(self):
+        with self.cv:
+            self.running = False
+            self.cv.notify()
+        self.thread.join()
+
+    def stats(self):
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return dict(requests=len(self.latencies), batches=self.batches, p50_ms=float(np.percentile(lat, 50) * 1e3),
+                    p99_ms=float(np.percentile(lat, 99) * 1e3))
+
+    # ---------------------------------------------------------------- serving thread
+    @staticmethod
+    def _bytes(n_poses: int) -> int:
+        # poses + outputs + the batch workspace's per-pose share (task buffers) + a fixed part
+        return n_poses * (48 + 4 + 1 + 2 * 16 * 256) + (96 << 20)
+
+    def _complete(self, slot):
+        ev, reqs, outs, nbytes, batch = self.busy[slot]
+        ev.synchronize()
+        code = int(batch.status.item())
+        now = time.perf_counter()
+        for r, o in zip(reqs, outs):
+            r.t_done = now
+            self.latencies.append(now - r.t_submit)
+            if code != 0:
+                r.future.set_exception(CbvhError(code, "device status"))
+            else:
+                r.future.set_result(o.numpy().copy())
+        self.busy[slot] = None
+        self.used -= nbytes
+
+    def _admit(self):
+        """Requests for the next batch: in arrival order, while memory and size allow."""
+        take, n, need = [], 0, 0
+        while self.pending:
+            r = self.pending[0]
+            rn = len(r.poses)
+            b = self._bytes(n + rn)
+            if take and (n + rn > self.max_poses or self.used + b > self.mem_budget):
+                break
+            if not take and self.used + b > self.mem_budget and any(self.busy):
+                break  # wait for memory to come back
+            take.append(self.pending.popleft())
+            n += rn
+            need = b
+        return take, need
+
+    def _launch(self, slot, reqs, nbytes):
+        torch = _torch()
+        stream = self.streams[slot]
+        with torch.cuda.stream(stream):
+            n_total = sum(len(r.poses) for r in reqs)
+            host = torch.empty((max(1, n_total), 12), dtype=torch.float32, pin_memory=True)
+            o = 0
+            for r in reqs:
+                host[o:o + len(r.poses)] = torch.from_numpy(r.poses)
+                o += len(r.poses)
+            dev = host.to(self.device, non_blocking=True)
+            items, o = [], 0
+            for r in reqs:
+                n = len(r.poses)
+                items.append(dict(A=self.models[r.env], B=self.models[r.robot], kind=r.kind,
+                                  poses=dev[o:o + n], early_exit=r.early_exit))
+                o += n
+            batch = Batch(items, device=self.device)
+            batch.launch(stream)
+            outs = []
+            for out in batch.outputs:
+                h = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+                h.copy_(out, non_blocking=True)
+                outs.append(h)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.busy[slot] = (ev, reqs, outs, nbytes, batch)
+        self.used += nbytes
+        self.batches += 1
+
+    def _loop(self):
+        try:
+            self._serve()
+        except BaseException as e:  # the loop itself failed: fail everything still queued
+            self.error = e
+            with self.cv:
+                self.running = False
+                waiting = list(self.pending)
+                self.pending.clear()
+            for r in waiting:
+                r.future.set_exception(e)
+            for b in self.busy:
+                if b is not None:
+                    for r in b[1]:
+                        if not r.future.done():
+                            r.future.set_exception(e)
+
+    def _serve(self):
+        torch = _torch()
+        torch.cuda.set_device(self.device)
+        while True:
+            with self.cv:
+                while self.running and not self.pending and not any(self.busy):
+                    self.cv.wait(0.01)
+                if not self.running and not self.pending and not any(self.busy):
+                    return
+            try:
+                for s, b in enumerate(self.busy):
+                    if b is not None and b[0].query():
+                        self._complete(s)
+                free = [s for s, b in enumerate(self.busy) if b is None]
+                if free:
+                    with self.cv:
+                        reqs, need = self._admit()
+                    if reqs:
+                        try:
+                            self._launch(free[0], reqs, need)
+                        except Exception as e:  # these requests never reached the device
+                            self.error = e
+                            for r in reqs:
+                                r.future.set_exception(e)
+                        continue
+                if any(self.busy):
+                    time.sleep(20e-6)
+            except Exception as e:  # fail the affected requests, keep serving
+                self.error = e
+                for s, b in enumerate(self.busy):
+                    if b is not None:
+                        for r in b[1]:
+                            if not r.future.done():
+                                r.future.set_exception(e)
+                        self.used -= b[3]
+                        self.busy[s] = None
