@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--poses", type=int, default=10000)
     ap.add_argument("--cpu-sample", type=int, default=0, help="poses in the oracle sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
+    ap.add_argument("--arm-configs", type=int, default=200000)
     return ap.parse_args()
 
 
@@ -172,6 +174,120 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+
+
+# ------------------------------------------------------------------ batched and served forms
+def _events_ms(fn, torch, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def arm_sweep(cb, torch, dev, n_configs):
+    """Motion-planning sweep: 6 arm links against a 1,026,400-triangle clutter scene, early-exit
+    CD for every configuration.  Batched (one set of persistent launches over all links,
+    replayed from a CUDA graph) against the plain traversal (one query per link and launch,
+    one warp per pose)."""
+    c = synth.C3(n_configs)
+    A = cb.BVH(*c["A"], 24, 8, 8, 16384, device=dev)
+    links = [cb.BVH(*l, 24, 8, 8, 16384, device=dev) for l in c["links"]]
+    LP = [torch.as_tensor(np.ascontiguousarray(c["link_poses"][:, i]), device=dev) for i in range(6)]
+    items = [dict(A=A, B=L, kind="collide", poses=P, early_exit=True) for L, P in zip(links, LP)]
+    batch = cb.Batch(items, device=dev)
+    outs = batch.run()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        batch.launch(s)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        batch.launch()
+    ms_batched = _events_ms(g.replay, torch)
+    collide_cfg = np.stack([o.cpu().numpy() for o in outs]).any(0)
+
+    def plain():
+        for L, P in zip(links, LP):
+            cb.collide(A, L, P, pairs=False, early_exit=True, check=False)
+    cb.set_option(cb.OPT_SPLIT, 0)
+    ms_plain = _events_ms(plain, torch, reps=2)
+    cb.set_option(cb.OPT_SPLIT, 1)
+    q = 6 * n_configs
+    return {"workload": f"6-link DH arm (5,120..40k tris per link) vs 1,026,400-tri clutter, {n_configs} configurations, "
+                        "early-exit CD, 24-DOP m=8 8-bit 16 KB treelets",
+            "link_queries": q, "configs_in_collision": int(collide_cfg.sum()),
+            "batched_link_queries_per_s": q / (ms_batched / 1e3), "batched_ms": ms_batched,
+            "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,
+            "speedup_vs_plain": ms_plain / ms_batched, "batched": "one graph-captured persistent launch set",
+            "plain": "one cbvh_collide per link, one warp per pose"}
+
+
+def serving(cb, torch, dev, models, rates=(100, 300, 1000), seconds=1.0, seed=2004):
+    """Request loop under open-loop Poisson arrivals: requests of log-uniform 1..4096 poses,
+    CD:PQ 1:1, robots (arm link, level-5 and level-3 spheres) against the terrain and the
+    clutter.  Reports p50/p99 latency and throughput; the plain form serves the same requests
+    one call at a time in arrival order."""
+    from paper_2012_05348_gb300.serve import Server
+    import threading
+    rng = np.random.default_rng(seed)
+    envs, robots = ["terrain", "clutter"], ["link", "sphere5", "sphere3"]
+    out = []
+    for rate in rates:
+        n_req = max(1, int(rate * seconds))
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        reqs = []
+        for i in range(n_req):
+            n = int(np.exp(rng.uniform(0, np.log(4096))))
+            env, rob = envs[i % 2], robots[i % 3]
+            P = synth.poses_box(n, seed=int(rng.integers(1 << 30)), lo=-1.5, hi=1.5)
+            if env == "terrain":
+                P[:, 11] = np.abs(P[:, 11]) * 0.3 + 0.5
+            reqs.append((env, rob, "collide" if i % 2 == 0 else "distance", P))
+        srv = Server(models, mem_budget=8 << 30, device=dev)
+        futs = []
+
+        def gen():
+            t0 = time.perf_counter()
+            t = 0.0
+            for (env, rob, kind, P), gap in zip(reqs, gaps):
+                t += gap
+                d = t0 + t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                futs.append(srv.submit(env, rob, kind, P, early_exit=False))
+        t_start = time.perf_counter()
+        th = threading.Thread(target=gen)
+        th.start()
+        th.join()
+        for f in futs:
+            f.result(timeout=600)
+        t_end = time.perf_counter()
+        srv.close()
+        st = srv.stats()
+        poses = sum(len(r[3]) for r in reqs)
+        # plain: the same requests, one call at a time
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for env, rob, kind, P in reqs:
+            Pd = torch.as_tensor(P, device=dev)
+            if kind == "collide":
+                cb.collide(models[env], models[rob], Pd, pairs=False).hit.cpu()
+            else:
+                cb.distance(models[env], models[rob], Pd).cpu()
+        t_plain = time.perf_counter() - t0
+        out.append({"rate_req_per_s": rate, "requests": n_req, "poses": poses, "batches": st["batches"],
+                    "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                    "served_poses_per_s": poses / (t_end - t_start), "plain_poses_per_s": poses / t_plain})
+    return out
+
+
 # ------------------------------------------------------------------ engine
 def main():
     args = parse()
@@ -251,6 +367,10 @@ def main():
         torch.cuda.synchronize()
     cb.profile_enable(False)
     prof = cb.profile_collect()
+    # our kernels per step: the traversal rounds of collide, its compaction (scan, scatter,
+    # sort), and the two traversal passes of distance
+    kernel_launches_cd = 6 + 3
+    kernel_launches_pq = 2 * 6
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -309,6 +429,14 @@ def main():
             traffic = json.load(open(tr_file)).get(dom[0])
         except (OSError, ValueError):
             traffic = None
+    extra = {}
+    if not args.no_extra:
+        extra["batched"] = arm_sweep(cb, torch, dev, args.arm_configs)
+        c3 = synth.C3(8)
+        models = {"terrain": A, "clutter": cb.BVH(*c3["A"], 24, 8, 8, 16384, device=dev),
+                  "link": cb.BVH(*c3["links"][3], 24, 8, 8, 16384, device=dev), "sphere5": B,
+                  "sphere3": cb.BVH(*synth.C1(1)["B"], 24, 8, 8, 16384, device=dev)}
+        extra["served"] = serving(cb, torch, dev, models)
     cpu = None
     if not args.no_cpu_baseline:
         rate, done, secs, cores = oracle_rate(c, args.cpu_sample)
@@ -342,8 +470,9 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "pose queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
-        "gpu_launches": K * 5,
+        "gpu_launches": K * (kernel_launches_cd + kernel_launches_pq),
     }
+    out.update(extra)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -950,7 +950,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
           break;
         }
       }
-      if ((expansions & 15) == 0) {
+      if ((expansions & (early ? 3 : 15)) == 0) {
         if (MODE == MODE_PQ) {
           float v = 0.f;
           if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
@@ -1256,6 +1256,9 @@ thread_local Profiler g_prof;
 // Rounds of a query and the expansion budget of a task in each (0 = none, last round).
 constexpr int kRounds = 6;
 constexpr int kBudget[kRounds] = {16, 32, 64, 128, 512, 0};
+// Early-exit collision queries stop a pose at its first hit; tasks handed on before then
+// waste work, so their budgets start high enough for most poses to finish in round 0.
+constexpr int kBudgetEarly[kRounds] = {4096, 8192, 16384, 32768, 65536, 0};
 constexpr int kMaxWarpsPerSM = 64;
 
 // Workspace layout: [0, 256) counters -- u64 pair count at 0, u64 stats[3] at 16, then per
@@ -1318,7 +1321,7 @@ TraverseFn traverse_fn(int K, bool batch = false) {
 // task count of every round); buf: the two task buffers; stacks: per-warp stacks.
 template <int MODE>
 int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint2 *stacks, uint32_t task_cap, int sms,
-                  cudaStream_t s, int slot = MODE) {
+                  cudaStream_t s, int slot = MODE, bool early_all = false) {
   const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
   const TraverseFn fn = traverse_fn<MODE>(p.A.K, p.items != nullptr);
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1347,7 +1350,7 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint2 
   for (int r = 0; r < rounds; ++r) {
     p.round = r;
     p.last_round = r == rounds - 1;
-    p.budget = kBudget[r];
+    p.budget = early_all ? kBudgetEarly[r] : kBudget[r];
     p.task_next = ctr + r;
     p.count_in = ctr + 8 + r;
     p.count_out = ctr + 8 + r + 1;
@@ -1367,9 +1370,10 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint2 
 // Single query: counters of pass k at ws + 64 (k + 1), buffers and stacks from the plan.
 template <int MODE>
 int launch_single(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t s, int pass = 0, int slot = MODE) {
+  const bool early = MODE == MODE_CD && (p.flags & CBVH_EARLY_EXIT);
   return launch_rounds<MODE>(p, reinterpret_cast<unsigned int *>(ws + 64 * (pass + 1)),
                              reinterpret_cast<uint4 *>(ws + w.tasks0), reinterpret_cast<uint4 *>(ws + w.tasks1),
-                             reinterpret_cast<uint2 *>(ws + w.stacks), w.task_cap, sms, s, slot);
+                             reinterpret_cast<uint2 *>(ws + w.stacks), w.task_cap, sms, s, slot, early);
 }
 
 int check_pair(const cbvh_bvh *A, const cbvh_bvh *B) {
@@ -1864,11 +1868,13 @@ extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t w
     uint2 *st = reinterpret_cast<uint2 *>(ws + b->o_stacks);
     if (g.mode == 0) {
       p.items = dev_items + g.first;
-      if (int rc = launch_rounds<MODE_CD>(p, ctr, t0, t1, st, b->task_cap, b->sms, s)) return rc;
+      bool all_early = true;
+      for (int k = 0; k < g.count; ++k) all_early &= (b->items[g.first + k].flags & CBVH_EARLY_EXIT) != 0;
+      if (int rc = launch_rounds<MODE_CD>(p, ctr, t0, t1, st, b->task_cap, b->sms, s, 0, all_early)) return rc;
     } else {
       Params c = p;
       c.items = dev_items + g.pre_first;
-      if (int rc = launch_rounds<MODE_CD>(c, ctr, t0, t1, st, b->task_cap, b->sms, s, 1)) return rc;
+      if (int rc = launch_rounds<MODE_CD>(c, ctr, t0, t1, st, b->task_cap, b->sms, s, 1, true)) return rc;
       p.items = dev_items + g.first;
       p.skip = ws + g.skip_off;
       if (int rc = launch_rounds<MODE_PQ>(p, ctr + 16, t0, t1, st, b->task_cap, b->sms, s)) return rc;
