@@ -179,13 +179,18 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
 
 /* Process-wide tuning options; the paper has no counterpart.
  *   CBVH_OPT_STAGE_BYTES: bytes of leading treelets of each hierarchy that every thread block
- *   copies into shared memory (TMA bulk copy) before a single query, 0..32768 (default
- *   16384; 0 disables).  Takes effect for queries issued afterwards. */
+ *   copies into shared memory (TMA bulk copy) before a single query, 0..32768 (default 0,
+ *   off: on the terrain workload the top treelets are L1-resident anyway and staging costs
+ *   occupancy).  Takes effect for queries issued afterwards. */
 #define CBVH_OPT_STAGE_BYTES 1
 /*   CBVH_OPT_SPLIT: work mapping.  1 (default): a pose's node-pair tree is split into tasks
  *   that later rounds spread over all warps (warp per node pair); 0: one round in which
  *   each warp traverses whole poses (warp per pose). */
 #define CBVH_OPT_SPLIT 2
+/*   CBVH_OPT_BUDGET0: node-pair expansions a task may run in round 0 before it hands the rest
+ *   of its work on (default 256; later rounds allow 2, 4, 8 and 32 times as many, the last
+ *   round no limit).  Queries that exit at the first hit use their own, larger budgets. */
+#define CBVH_OPT_BUDGET0 3
 int cbvh_set_option(int option, int64_t value);
 
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests

@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
-           "set_option", "OPT_STAGE_BYTES", "OPT_SPLIT", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
+           "set_option", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
 LIB_PATH = _build.LIB
 EARLY_EXIT = 1
@@ -168,6 +168,7 @@ class BVH:
 
 OPT_STAGE_BYTES = 1
 OPT_SPLIT = 2
+OPT_BUDGET0 = 3
 
 
 def set_option(option: int, value: int) -> None:

@@ -16,10 +16,11 @@ import os
 
 import numpy as np
 
-from . import BVH, OPT_SPLIT, OPT_STAGE_BYTES, collide, distance, profile_collect, profile_enable, set_option
+from . import (BVH, OPT_BUDGET0, OPT_SPLIT, OPT_STAGE_BYTES, collide, distance, profile_collect, profile_enable,
+               set_option)
 
 DEFAULT_SPACE = dict(branching=(4, 8, 16), treelet_bytes=(4096, 16384, 65536), quant_bits=(8, 16),
-                     stage_bytes=(0, 16384), split=(1, 0))
+                     stage_bytes=(0, 16384), split=(1, 0), budget0=(64, 256, 1024))
 
 
 def mesh_key(verts_a, tris_a, verts_b, tris_b, k: int, kind: str) -> str:
@@ -64,17 +65,20 @@ def autotune(mesh_a, mesh_b, poses, k: int = 24, kind: str = "collide", early_ex
             B = BVH(*mesh_b, k, m, bits, tb, device=device)
         except Exception:  # budget too small for this branching and k
             continue
-        for stage, split in itertools.product(space["stage_bytes"], space["split"]):
+        for stage, split, b0 in itertools.product(space["stage_bytes"], space["split"], space["budget0"]):
+            if not split and b0 != space["budget0"][0]:
+                continue  # the budget only matters when tasks are handed on
             set_option(OPT_STAGE_BYTES, stage)
             set_option(OPT_SPLIT, split)
+            set_option(OPT_BUDGET0, b0)
             if kind == "collide":
                 fn = lambda: collide(A, B, poses, pairs=False, early_exit=early_exit)  # noqa: E731
             else:
                 fn = lambda: distance(A, B, poses)  # noqa: E731
             ms = _time(fn, reps)
-            trials.append((dict(branching=m, treelet_bytes=tb, quant_bits=bits, stage_bytes=stage, split=split), ms))
-    set_option(OPT_STAGE_BYTES, 16384)
-    set_option(OPT_SPLIT, 1)
+            trials.append((dict(branching=m, treelet_bytes=tb, quant_bits=bits, stage_bytes=stage, split=split,
+                                budget0=b0), ms))
+    apply({})
     best = min(trials, key=lambda t: t[1])[0]
     if cache:
         store[key] = dict(best=best, trials=trials)
@@ -87,6 +91,7 @@ def autotune(mesh_a, mesh_b, poses, k: int = 24, kind: str = "collide", early_ex
 
 def apply(config: dict) -> None:
     """Set the launch options of a tuned configuration (the hierarchy parameters are used when
-    building the BVHs)."""
-    set_option(OPT_STAGE_BYTES, int(config.get("stage_bytes", 16384)))
+    building the BVHs); an empty dict restores the defaults."""
+    set_option(OPT_STAGE_BYTES, int(config.get("stage_bytes", 0)))
     set_option(OPT_SPLIT, int(config.get("split", 1)))
+    set_option(OPT_BUDGET0, int(config.get("budget0", 256)))

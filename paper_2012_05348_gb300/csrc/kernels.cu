@@ -499,7 +499,7 @@ enum { MODE_CD = 0, MODE_PQ = 1 };
 // Pose cache layout (floats): R[9], t[3], then per A-direction j: u[3], |u|[3], s_lo, s_hi, eta
 constexpr int kPoseJ = 9;
 __device__ __forceinline__ float *pose_dir(float *pc, int j) { return pc + 12 + kPoseJ * j; }
-constexpr int kStageBytesDefault = 16384;  // per hierarchy and block: leading treelets staged in shared memory
+constexpr int kStageBytesDefault = 0;  // per hierarchy and block: leading treelets staged in shared memory
 
 // Conservative interval of d_j . (R x + t) over B-member i: the exact posed triangle when the
 // member is a leaf, otherwise its decoded axis box.  q = pose_dir(pc, j).
@@ -1165,6 +1165,7 @@ int align16(int x) { return (x + 15) & ~15; }
 // Process-wide tuning options (cbvh_set_option).
 std::atomic<int> g_stage_bytes{kStageBytesDefault};
 std::atomic<int> g_split{1};  // 1: node-pair tasks handed on between rounds; 0: one warp per pose
+std::atomic<int> g_budget0{256};  // expansion budget of a task in round 0 (later rounds scale it)
 
 // Per-warp slice layout for A's direction count, the deepest nodes below a treelet root on
 // either side and a stack bound; no staged treelets.
@@ -1350,7 +1351,7 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint2 
   for (int r = 0; r < rounds; ++r) {
     p.round = r;
     p.last_round = r == rounds - 1;
-    p.budget = early_all ? kBudgetEarly[r] : kBudget[r];
+    p.budget = early_all ? kBudgetEarly[r] : (kBudget[r] / 16) * g_budget0.load();
     p.task_next = ctr + r;
     p.count_in = ctr + 8 + r;
     p.count_out = ctr + 8 + r + 1;
@@ -1888,6 +1889,11 @@ extern "C" int cbvh_set_option(int option, int64_t value) {
   if (option == CBVH_OPT_STAGE_BYTES) {
     if (value < 0 || value > 32768) return cbvh::fail(CBVH_ERR_ARG, "stage bytes must be in [0, 32768]");
     g_stage_bytes.store((int)value);
+    return CBVH_OK;
+  }
+  if (option == CBVH_OPT_BUDGET0) {
+    if (value < 1 || value > (1 << 20)) return cbvh::fail(CBVH_ERR_ARG, "budget must be in [1, 2^20]");
+    g_budget0.store((int)value);
     return CBVH_OK;
   }
   if (option == CBVH_OPT_SPLIT) {

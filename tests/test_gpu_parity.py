@@ -282,3 +282,28 @@ def test_c2_full_size_sampled_against_oracle(cb, c2):
         if len(pairs[p]) > 1:
             key = pairs[p][:, 0].astype(np.int64) * (1 << 32) + pairs[p][:, 1]
             assert (np.diff(key) > 0).all()
+
+
+@pytest.mark.parametrize("stage,split,budget0", [(16384, 1, 16), (32768, 1, 256), (0, 0, 256)])
+def test_launch_options_keep_results(cb, c1, c2, stage, split, budget0):
+    """Treelet staging in shared memory (TMA bulk copies), the warp-per-pose mapping and the
+    task budget change how the work is scheduled, never the result."""
+    import torch
+    P1 = _gpu(c1["P"])
+    P2 = _gpu(c2["c"]["poses"][:1500])
+    ref = (cb.collide(c1["A"], c1["B"], P1), cb.distance(c1["A"], c1["B"], P1).cpu().numpy(),
+           cb.collide(c2["A"], c2["B"], P2), cb.distance(c2["A"], c2["B"], P2).cpu().numpy())
+    cb.set_option(cb.OPT_STAGE_BYTES, stage)
+    cb.set_option(cb.OPT_SPLIT, split)
+    cb.set_option(cb.OPT_BUDGET0, budget0)
+    try:
+        got = (cb.collide(c1["A"], c1["B"], P1), cb.distance(c1["A"], c1["B"], P1).cpu().numpy(),
+               cb.collide(c2["A"], c2["B"], P2), cb.distance(c2["A"], c2["B"], P2).cpu().numpy())
+    finally:
+        cb.set_option(cb.OPT_STAGE_BYTES, 0)
+        cb.set_option(cb.OPT_SPLIT, 1)
+        cb.set_option(cb.OPT_BUDGET0, 256)
+    for r, g in ((ref[0], got[0]), (ref[2], got[2])):
+        assert torch.equal(r.hit, g.hit) and torch.equal(r.offsets, g.offsets) and torch.equal(r.pairs, g.pairs)
+    assert np.allclose(ref[1], got[1], rtol=0, atol=1e-5 * c1["D"])
+    assert np.allclose(ref[3], got[3], rtol=0, atol=1e-5 * c2["D"])
