@@ -120,9 +120,12 @@ int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64
                  void *workspace, int64_t workspace_bytes, int32_t *status, void *stream);
 
 /* Proximity query: dist[p] = minimum distance between the triangles of A and those of
- * R_p B + t_p (0 when they intersect), by branch-and-bound Algorithm 1 with slab-gap lower
- * bounds.  A collision pass with early exit runs first and settles the intersecting poses
- * at 0.  FP32; accurate to a few ulps of the scene size. */
+ * R_p B + t_p (0 when they intersect), by branch-and-bound Algorithm 1.  A node pair is
+ * pruned when its lower bound reaches the best distance found: the larger of the widest
+ * slab gap over |d_j| and the distance between the two axis boxes (root of the summed
+ * squared x, y and z gaps), both rounded down.  A collision pass with early exit runs
+ * first and settles the intersecting poses at 0.  FP32; accurate to a few ulps of the
+ * scene size. */
 int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist, void *workspace,
                   int64_t workspace_bytes, int32_t *status, void *stream);
 
@@ -191,6 +194,20 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
  *   of its work on (default 256; later rounds allow 2, 4, 8 and 32 times as many, the last
  *   round no limit).  Queries that exit at the first hit use their own, larger budgets. */
 #define CBVH_OPT_BUDGET0 3
+/*   CBVH_OPT_TREELET_PACKING: how cbvh_build forms treelets (Sec. III-B sizes them to the
+ *   cache; how nodes are grouped is not given).  Both keep whole sibling groups together and
+ *   give each treelet an absolute root, so the blob format and every query result are the
+ *   same; footprint and decode-chain length differ.  Takes effect for builds started
+ *   afterwards; the value is recorded in the blob header (bytes 44..47).
+ *     CBVH_PACK_TOP_DOWN (default): greedy breadth-first growth from each root; a sibling
+ *     group that does not fit makes each of its nodes a new root.  Leaves many small
+ *     treelets near the leaves.
+ *     CBVH_PACK_BOTTOM_UP: a node's children join its treelet while the node and all the
+ *     nodes its children still carry fit one treelet; otherwise each child roots a treelet.
+ *     Fewer, fuller treelets and fewer absolute roots; deeper chains below a root. */
+#define CBVH_OPT_TREELET_PACKING 4
+#define CBVH_PACK_TOP_DOWN 0
+#define CBVH_PACK_BOTTOM_UP 1
 int cbvh_set_option(int option, int64_t value);
 
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests

@@ -17,6 +17,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
+# Treelet formation: 0 grows treelets top-down (breadth-first from each root), 1 packs them
+# bottom-up (a subtree joins its parent's treelet while it fits).  Blobs are compared with
+# the library's at equal packing.
+PACKING_TOP_DOWN, PACKING_BOTTOM_UP = 0, 1
+PACKING_DEFAULT = PACKING_TOP_DOWN
 
 
 def build(force: bool = False) -> str:
@@ -37,7 +42,7 @@ def lib():
         L = C.CDLL(_LIB)
         P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
         L.or_last_error.restype = C.c_char_p
-        L.or_build.argtypes = [P, I64, P, I64, I32, I32, I32, I32, C.POINTER(C.c_void_p)]
+        L.or_build.argtypes = [P, I64, P, I64, I32, I32, I32, I32, I32, C.POINTER(C.c_void_p)]
         L.or_build.restype = I32
         L.or_free.argtypes = [P]
         L.or_info.argtypes = [P, P]
@@ -101,13 +106,13 @@ class OracleError(RuntimeError):
 class BVH:
     """The oracle's BVH of one mesh: its tree, exact lattice bounds, encoding and blob."""
 
-    def __init__(self, verts, tris, k: int, m: int, bits: int, treelet_bytes: int):
+    def __init__(self, verts, tris, k: int, m: int, bits: int, treelet_bytes: int, packing: int = PACKING_DEFAULT):
         L = lib()
         self.verts = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
         self.tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
         h = C.c_void_p()
         rc = L.or_build(_p(self.verts), len(self.verts), _p(self.tris), len(self.tris), k, m, bits,
-                        treelet_bytes, C.byref(h))
+                        treelet_bytes, packing, C.byref(h))
         if rc != 0:
             raise OracleError(rc, L.or_last_error().decode())
         self._h = h
@@ -115,7 +120,7 @@ class BVH:
         L.or_info(h, _p(info))
         (self.n_nodes, self.n_treelets, self.e, self.depth, self.blob_bytes, self.lbits,
          self.max_tdepth, self.K, self.rec_bytes, self.root_bytes) = (int(x) for x in info)
-        self.k, self.m, self.bits, self.treelet_bytes = k, m, bits, treelet_bytes
+        self.k, self.m, self.bits, self.treelet_bytes, self.packing = k, m, bits, treelet_bytes, packing
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

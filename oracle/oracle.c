@@ -142,6 +142,7 @@ typedef struct {
   int32_t **tlet_nodes;
   int lbits, max_tdepth;
   int rec_bytes, root_bytes;
+  int packing; /* 0: treelets grown top-down; 1: packed bottom-up (see encode) */
   uint8_t *blob;
   int64_t blob_bytes;
 } or_bvh;
@@ -259,8 +260,9 @@ static int encode(or_bvh *h);
 
 /* Build the BVH of a triangle mesh and its compressed blob. */
 int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, int k, int m, int bits,
-             int treelet_bytes, or_bvh **out) {
+             int treelet_bytes, int packing, or_bvh **out) {
   *out = NULL;
+  if (packing != 0 && packing != 1) return fail(OR_ERR_ARG, "packing must be 0 or 1");
   if (k != 6 && k != 18 && k != 24 && k != 26) return fail(OR_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (m != 2 && m != 4 && m != 8 && m != 16) return fail(OR_ERR_ARG, "branching must be 2, 4, 8 or 16");
   if (bits != 0 && bits != 8 && bits != 16) return fail(OR_ERR_ARG, "quant_bits must be 0, 8 or 16");
@@ -273,6 +275,7 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   h->m = m;
   h->bits = bits;
   h->budget = treelet_bytes;
+  h->packing = packing;
   h->nv = nv;
   h->nt = nt;
   h->root_bytes = 8 + 8 * h->K;
@@ -459,6 +462,66 @@ static uint32_t f2u(float f) {
   return u;
 }
 
+/* Treelets packed bottom-up (Sec. III-B: treelets sized to the cache).  Going from the
+ * deepest nodes up, each node carries the nodes of its subtree not yet cut off.  A node's
+ * children stay in its treelet when the node plus everything its children carry still fits
+ * one treelet (16 B header, the absolute root record, the other nodes as delta records);
+ * otherwise all of its children become roots of treelets of their own.  The treelets are
+ * the tree's root and every such child, numbered in node order (so siblings get consecutive
+ * numbers); a treelet's nodes are listed breadth-first from its root. */
+static int pack_bottom_up(or_bvh *h) {
+  int64_t nn = h->nn;
+  int64_t fit = (h->budget - 16 - h->root_bytes) / h->rec_bytes + 1; /* nodes per treelet */
+  int64_t *carry = (int64_t *)malloc(sizeof(int64_t) * nn);
+  for (int64_t x = nn - 1; x >= 0; --x) {
+    int64_t sum = 1;
+    for (int c = 0; c < h->nchild[x]; ++c) sum += carry[h->first[x] + c];
+    if (sum <= fit) {
+      carry[x] = sum;
+    } else {
+      carry[x] = 1;
+      h->ext[x] = 1;
+    }
+  }
+  free(carry);
+  int64_t nroot = 0;
+  for (int64_t x = 0; x < nn; ++x)
+    if (x == 0 || h->ext[h->parent[x]]) ++nroot;
+  h->ntlet = nroot;
+  h->tlet_root = (int32_t *)malloc(sizeof(int32_t) * nroot);
+  h->tlet_count = (int32_t *)malloc(sizeof(int32_t) * nroot);
+  h->tlet_nodes = (int32_t **)malloc(sizeof(int32_t *) * nroot);
+  int32_t *tlet_of = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int64_t t = 0;
+  for (int64_t x = 0; x < nn; ++x)
+    if (x == 0 || h->ext[h->parent[x]]) {
+      tlet_of[x] = (int32_t)t;
+      h->tlet_root[t++] = (int32_t)x;
+    }
+  for (int64_t x = 0; x < nn; ++x)
+    if (h->ext[x]) h->child_tlet[x] = tlet_of[h->first[x]];
+  free(tlet_of);
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * nn);
+  for (t = 0; t < nroot; ++t) {
+    int64_t head = 0, tail = 0;
+    queue[tail++] = h->tlet_root[t];
+    while (head < tail) {
+      int32_t x = queue[head++];
+      if (!h->ext[x])
+        for (int c = 0; c < h->nchild[x]; ++c) queue[tail++] = h->first[x] + c;
+    }
+    h->tlet_count[t] = (int32_t)tail;
+    h->tlet_nodes[t] = (int32_t *)malloc(sizeof(int32_t) * tail);
+    for (int64_t l = 0; l < tail; ++l) {
+      h->tlet_nodes[t][l] = queue[l];
+      h->tlet[queue[l]] = (int32_t)t;
+      h->local[queue[l]] = (int32_t)l;
+    }
+  }
+  free(queue);
+  return 0;
+}
+
 static int encode(or_bvh *h) {
   int64_t nn = h->nn;
   int K = h->K;
@@ -468,66 +531,70 @@ static int encode(or_bvh *h) {
   h->child_tlet = (int32_t *)malloc(sizeof(int32_t) * nn);
   for (int64_t i = 0; i < nn; ++i) h->child_tlet[i] = -1;
 
-  /* Treelets (Sec. III-B): greedy BFS from each treelet root, adding whole sibling groups
-   * while the treelet header, the absolute root record and the delta records fit the byte
-   * budget.  A group that does not fit turns each of its nodes into the root of a new
-   * treelet; new treelets are numbered in the order they are created. */
-  int64_t cap = 1024;
-  h->tlet_root = (int32_t *)malloc(sizeof(int32_t) * cap);
-  h->tlet_root[0] = 0;
-  h->ntlet = 1;
-  int64_t tcap = 1024;
-  h->tlet_count = (int32_t *)malloc(sizeof(int32_t) * tcap);
-  h->tlet_nodes = (int32_t **)malloc(sizeof(int32_t *) * tcap);
-  int32_t *bfs = (int32_t *)malloc(sizeof(int32_t) * nn);
-  for (int64_t t = 0; t < h->ntlet; ++t) {
-    if (t >= tcap) {
-      tcap *= 2;
-      h->tlet_count = (int32_t *)realloc(h->tlet_count, sizeof(int32_t) * tcap);
-      h->tlet_nodes = (int32_t **)realloc(h->tlet_nodes, sizeof(int32_t *) * tcap);
-    }
-    int32_t r = h->tlet_root[t];
-    int64_t size = 16 + h->root_bytes;
-    int64_t cnt = 0, ncap = 64;
-    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * ncap);
-    mem[cnt] = r;
-    h->tlet[r] = (int32_t)t;
-    h->local[r] = (int32_t)cnt++;
-    int64_t bh = 0, bt = 0;
-    bfs[bt++] = r;
-    while (bh < bt) {
-      int32_t x = bfs[bh++];
-      int nc = h->nchild[x];
-      if (nc == 0) continue;
-      if (size + (int64_t)nc * h->rec_bytes <= h->budget) {
-        size += (int64_t)nc * h->rec_bytes;
-        for (int c = 0; c < nc; ++c) {
-          int32_t y = h->first[x] + c;
-          if (cnt == ncap) {
-            ncap *= 2;
-            mem = (int32_t *)realloc(mem, sizeof(int32_t) * ncap);
+  if (h->packing == 1) {
+    if (pack_bottom_up(h)) return 1;
+  } else {
+    /* Treelets (Sec. III-B): greedy BFS from each treelet root, adding whole sibling groups
+     * while the treelet header, the absolute root record and the delta records fit the byte
+     * budget.  A group that does not fit turns each of its nodes into the root of a new
+     * treelet; new treelets are numbered in the order they are created. */
+    int64_t cap = 1024;
+    h->tlet_root = (int32_t *)malloc(sizeof(int32_t) * cap);
+    h->tlet_root[0] = 0;
+    h->ntlet = 1;
+    int64_t tcap = 1024;
+    h->tlet_count = (int32_t *)malloc(sizeof(int32_t) * tcap);
+    h->tlet_nodes = (int32_t **)malloc(sizeof(int32_t *) * tcap);
+    int32_t *bfs = (int32_t *)malloc(sizeof(int32_t) * nn);
+    for (int64_t t = 0; t < h->ntlet; ++t) {
+      if (t >= tcap) {
+        tcap *= 2;
+        h->tlet_count = (int32_t *)realloc(h->tlet_count, sizeof(int32_t) * tcap);
+        h->tlet_nodes = (int32_t **)realloc(h->tlet_nodes, sizeof(int32_t *) * tcap);
+      }
+      int32_t r = h->tlet_root[t];
+      int64_t size = 16 + h->root_bytes;
+      int64_t cnt = 0, ncap = 64;
+      int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * ncap);
+      mem[cnt] = r;
+      h->tlet[r] = (int32_t)t;
+      h->local[r] = (int32_t)cnt++;
+      int64_t bh = 0, bt = 0;
+      bfs[bt++] = r;
+      while (bh < bt) {
+        int32_t x = bfs[bh++];
+        int nc = h->nchild[x];
+        if (nc == 0) continue;
+        if (size + (int64_t)nc * h->rec_bytes <= h->budget) {
+          size += (int64_t)nc * h->rec_bytes;
+          for (int c = 0; c < nc; ++c) {
+            int32_t y = h->first[x] + c;
+            if (cnt == ncap) {
+              ncap *= 2;
+              mem = (int32_t *)realloc(mem, sizeof(int32_t) * ncap);
+            }
+            mem[cnt] = y;
+            h->tlet[y] = (int32_t)t;
+            h->local[y] = (int32_t)cnt++;
+            bfs[bt++] = y;
           }
-          mem[cnt] = y;
-          h->tlet[y] = (int32_t)t;
-          h->local[y] = (int32_t)cnt++;
-          bfs[bt++] = y;
-        }
-      } else {
-        h->ext[x] = 1;
-        h->child_tlet[x] = (int32_t)h->ntlet;
-        for (int c = 0; c < nc; ++c) {
-          if (h->ntlet == cap) {
-            cap *= 2;
-            h->tlet_root = (int32_t *)realloc(h->tlet_root, sizeof(int32_t) * cap);
+        } else {
+          h->ext[x] = 1;
+          h->child_tlet[x] = (int32_t)h->ntlet;
+          for (int c = 0; c < nc; ++c) {
+            if (h->ntlet == cap) {
+              cap *= 2;
+              h->tlet_root = (int32_t *)realloc(h->tlet_root, sizeof(int32_t) * cap);
+            }
+            h->tlet_root[h->ntlet++] = h->first[x] + c;
           }
-          h->tlet_root[h->ntlet++] = h->first[x] + c;
         }
       }
+      h->tlet_count[t] = (int32_t)cnt;
+      h->tlet_nodes[t] = mem;
     }
-    h->tlet_count[t] = (int32_t)cnt;
-    h->tlet_nodes[t] = mem;
+    free(bfs);
   }
-  free(bfs);
 
   int maxn = 1;
   for (int64_t t = 0; t < h->ntlet; ++t)
@@ -611,7 +678,7 @@ static int encode(or_bvh *h) {
   put32(B + 32, (uint32_t)h->root_bytes);
   put32(B + 36, (uint32_t)h->budget);
   put32(B + 40, (uint32_t)h->tree_depth);
-  put32(B + 44, 0);
+  put32(B + 44, (uint32_t)h->packing);
   put64(B + 48, (uint64_t)off_tris);
   put64(B + 56, (uint64_t)total);
   for (int64_t t = 0; t <= h->ntlet; ++t) put64(B + off_tab + 8 * t, (uint64_t)toff[t]);
@@ -1109,16 +1176,20 @@ static int bv_overlap(tctx *c, int32_t a, int32_t b) {
     if (slab_gap(c, a, b, j) > 0) return 0;
   return 1;
 }
-/* Lower bound on the distance between the contents of a and b: max_j gap_j / |d_j|. */
+/* Lower bound on the distance between the contents of a and b, the larger of two valid
+ * bounds: max_j gap_j / |d_j| (the two contents lie in slabs gap_j / |d_j| apart), and
+ * sqrt(gap_x^2 + gap_y^2 + gap_z^2) over the three axis directions, the distance between
+ * A's axis box and the axis-aligned box around b's moved box, which contain the contents. */
 static double bv_lower(tctx *c, int32_t a, int32_t b) {
   c->bv_tests++;
-  double lb = 0.0;
+  double lb = 0.0, box2 = 0.0;
   for (int j = 0; j < c->A->K; ++j) {
     double g = slab_gap(c, a, b, j);
     double n = norm3((const double[3]){OR_DIR[j][0], OR_DIR[j][1], OR_DIR[j][2]});
     if (g / n > lb) lb = g / n;
+    if (j < 3 && g > 0) box2 += g * g;
   }
-  return lb;
+  return fmax(lb, sqrt(box2));
 }
 
 static void tri_A(const or_bvh *A, int32_t t, double T[3][3]) {

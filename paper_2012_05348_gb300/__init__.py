@@ -19,7 +19,8 @@ import numpy as np
 from . import _build
 
 __all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
-           "set_option", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
+           "set_option", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
+           "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
 LIB_PATH = _build.LIB
 EARLY_EXIT = 1
@@ -169,10 +170,13 @@ class BVH:
 OPT_STAGE_BYTES = 1
 OPT_SPLIT = 2
 OPT_BUDGET0 = 3
+OPT_TREELET_PACKING = 4
+PACK_TOP_DOWN, PACK_BOTTOM_UP = 0, 1
 
 
 def set_option(option: int, value: int) -> None:
-    """cbvh_set_option: process-wide tuning options (OPT_STAGE_BYTES)."""
+    """cbvh_set_option: process-wide tuning options (OPT_STAGE_BYTES, OPT_SPLIT, OPT_BUDGET0,
+    OPT_TREELET_PACKING)."""
     _check(_load().cbvh_set_option(int(option), int(value)))
 
 

@@ -8,14 +8,16 @@
 //   * predictor-corrector deltas (abstract; Sec. III-B, "predictors based on the delta to
 //     the parent nodes"): a node is predicted by its parent's decoded interval and
 //     corrected by b-bit unsigned deltas that round outward;
-//   * treelets (Sec. III-B, "clustering BVHs into a smaller parts"): greedy breadth-first
-//     clusters of whole sibling groups within a byte budget, each with an absolute root so
-//     that any treelet is randomly accessible (abstract).
+//   * treelets (Sec. III-B, "clustering BVHs into a smaller parts"): clusters of whole
+//     sibling groups within a byte budget, grown top-down (breadth-first from each root) or
+//     packed bottom-up (CBVH_OPT_TREELET_PACKING), each with an absolute root so that any
+//     treelet is randomly accessible (abstract).
 //
 // Blob layout (little endian; offsets from the blob start):
 //   [0, 64)     header: magic 'CBVH', version, k, K, m, bits, lbits, max treelet depth,
 //               e, n_tris, n_nodes, n_treelets, record bytes, root record bytes, treelet
-//               budget, tree depth, 0, offset of the triangle table, total bytes
+//               budget, tree depth, treelet packing, offset of the triangle table,
+//               total bytes
 //   [64, ...)   u64 treelet offsets [n_treelets + 1]
 //   treelets    16-byte aligned: {u32 node count, u32 blob-order index of the root, 0, 0},
 //               the root record, then fixed-size records in treelet BFS order
@@ -27,6 +29,7 @@
 //         int32 lattice values at a treelet root, b-bit correctors elsewhere, or FP32
 //         values (lo rounded down, hi rounded up) everywhere when quant_bits = 0.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -328,34 +331,77 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   }
   for (const Node &nd : B.nodes) h->depth = std::max(h->depth, nd.depth);
 
-  // ---- treelets: greedy BFS of whole sibling groups inside the byte budget ----
+  // ---- treelets ----
   std::vector<int32_t> tlet(nn), local(nn), child_tlet(nn, -1);
   std::vector<uint8_t> ext(nn, 0);
   std::vector<int32_t> roots{0};
   std::vector<std::vector<int32_t>> members;
-  for (size_t t = 0; t < roots.size(); ++t) {
-    std::vector<int32_t> mem{roots[t]};
-    tlet[roots[t]] = (int32_t)t;
-    local[roots[t]] = 0;
-    int64_t used_bytes = 16 + h->root_bytes;
-    for (size_t i = 0; i < mem.size(); ++i) {  // `mem` doubles as the BFS queue
-      const Node &nd = B.nodes[mem[i]];
-      if (nd.count == 0) continue;
-      int64_t need = (int64_t)nd.count * h->rec_bytes;
-      if (used_bytes + need <= treelet_bytes) {
-        used_bytes += need;
-        for (int c = 0; c < nd.count; ++c) {
-          tlet[nd.first + c] = (int32_t)t;
-          local[nd.first + c] = (int32_t)mem.size();
-          mem.push_back(nd.first + c);
-        }
-      } else {
-        ext[mem[i]] = 1;
-        child_tlet[mem[i]] = (int32_t)roots.size();
-        for (int c = 0; c < nd.count; ++c) roots.push_back(nd.first + c);
+  const int packing = cbvh::treelet_packing();
+  if (packing == CBVH_PACK_BOTTOM_UP) {
+    // Bottom-up: `carry` counts the nodes of a subtree not yet cut off.  A node keeps its
+    // children while it and everything they carry fit one treelet; else every child roots
+    // a treelet of its own.  Treelets are numbered in node (BFS) order of their roots.
+    const int64_t fit = (treelet_bytes - 16 - h->root_bytes) / h->rec_bytes + 1;
+    std::vector<int64_t> carry(nn, 1);
+    for (int64_t x = nn - 1; x >= 0; --x) {
+      const Node &nd = B.nodes[x];
+      int64_t c = 1;
+      for (int i = 0; i < nd.count; ++i) c += carry[nd.first + i];
+      if (c <= fit)
+        carry[x] = c;
+      else
+        ext[x] = 1;
+    }
+    std::vector<int32_t> tl_of(nn, -1);
+    tl_of[0] = 0;
+    for (int64_t x = 1; x < nn; ++x)
+      if (ext[B.nodes[x].parent]) {
+        tl_of[x] = (int32_t)roots.size();
+        roots.push_back((int32_t)x);
+      }
+    members.resize(roots.size());
+    for (size_t t = 0; t < roots.size(); ++t) {
+      std::vector<int32_t> &mem = members[t];
+      mem.push_back(roots[t]);
+      for (size_t i = 0; i < mem.size(); ++i) {
+        const int32_t x = mem[i];
+        tlet[x] = (int32_t)t;
+        local[x] = (int32_t)i;
+        const Node &nd = B.nodes[x];
+        if (ext[x])
+          child_tlet[x] = tl_of[nd.first];
+        else
+          for (int c = 0; c < nd.count; ++c) mem.push_back(nd.first + c);
       }
     }
-    members.push_back(std::move(mem));
+  } else {
+    // Top-down: greedy BFS from each root adding whole sibling groups inside the budget; a
+    // group that does not fit makes each of its nodes a new treelet root, numbered in the
+    // order of creation.
+    for (size_t t = 0; t < roots.size(); ++t) {
+      std::vector<int32_t> mem{roots[t]};
+      tlet[roots[t]] = (int32_t)t;
+      local[roots[t]] = 0;
+      int64_t used_bytes = 16 + h->root_bytes;
+      for (size_t i = 0; i < mem.size(); ++i) {  // `mem` doubles as the BFS queue
+        const Node &nd = B.nodes[mem[i]];
+        if (nd.count == 0) continue;
+        int64_t need = (int64_t)nd.count * h->rec_bytes;
+        if (used_bytes + need <= treelet_bytes) {
+          used_bytes += need;
+          for (int c = 0; c < nd.count; ++c) {
+            tlet[nd.first + c] = (int32_t)t;
+            local[nd.first + c] = (int32_t)mem.size();
+            mem.push_back(nd.first + c);
+          }
+        } else {
+          ext[mem[i]] = 1;
+          child_tlet[mem[i]] = (int32_t)roots.size();
+          for (int c = 0; c < nd.count; ++c) roots.push_back(nd.first + c);
+        }
+      }
+      members.push_back(std::move(mem));
+    }
   }
   const int64_t ntl = (int64_t)roots.size();
   size_t maxn = 1;
@@ -482,7 +528,7 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   w32(b, 32, (uint32_t)h->root_bytes);
   w32(b, 36, (uint32_t)treelet_bytes);
   w32(b, 40, (uint32_t)h->depth);
-  w32(b, 44, 0);
+  w32(b, 44, (uint32_t)packing);
   w64(b, 48, (uint64_t)h->off_tris);
   w64(b, 56, (uint64_t)total);
   for (int64_t t = 0; t <= ntl; ++t) w64(b, 64 + 8 * t, (uint64_t)toff[t]);
@@ -525,7 +571,10 @@ extern "C" int cbvh_blob_host(const cbvh_bvh *h, const uint8_t **blob, int64_t *
 namespace cbvh {
 namespace {
 thread_local std::string g_err;
-}
+std::atomic<int> g_packing{CBVH_PACK_TOP_DOWN};
+}  // namespace
+void set_treelet_packing(int p) { g_packing.store(p); }
+int treelet_packing() { return g_packing.load(); }
 int fail(int code, const std::string &msg) {
   g_err = msg;
   return code;

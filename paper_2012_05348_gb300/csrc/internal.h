@@ -27,4 +27,7 @@ namespace cbvh {
 // Records a message for cbvh_last_error() and returns `code`.
 int fail(int code, const std::string &msg);
 void clear_error();
+// Treelet formation used by cbvh_build (CBVH_PACK_*), set by cbvh_set_option.
+void set_treelet_packing(int packing);
+int treelet_packing();
 }  // namespace cbvh

@@ -867,12 +867,20 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
 #pragma unroll
             for (int d = 0; d < KA; ++d) keep &= (al[d] <= ph[d]) & (pl[d] <= ah[d]);
           } else {
+            // two lower bounds, all rounded down: the widest slab gap over |d|, and the
+            // distance between the axis boxes, sqrt of the squared gaps along x, y and z
             lb = 0.f;
+            float box2 = 0.f;
 #pragma unroll
             for (int d = 0; d < KA; ++d) {
               const float g = fmaxf(__fsub_rd(al[d], ph[d]), __fsub_rd(pl[d], ah[d]));
               lb = fmaxf(lb, __fmul_rd(g, p.invn[d]));
+              if (d < 3) {
+                const float gp = fmaxf(g, 0.f);
+                box2 = __fmaf_rd(gp, gp, box2);
+              }
             }
+            lb = fmaxf(lb, __fsqrt_rd(box2));
             keep = lb < best;
           }
         }
@@ -1899,6 +1907,12 @@ extern "C" int cbvh_set_option(int option, int64_t value) {
   if (option == CBVH_OPT_SPLIT) {
     if (value != 0 && value != 1) return cbvh::fail(CBVH_ERR_ARG, "split must be 0 or 1");
     g_split.store((int)value);
+    return CBVH_OK;
+  }
+  if (option == CBVH_OPT_TREELET_PACKING) {
+    if (value != CBVH_PACK_TOP_DOWN && value != CBVH_PACK_BOTTOM_UP)
+      return cbvh::fail(CBVH_ERR_ARG, "treelet packing must be CBVH_PACK_TOP_DOWN or CBVH_PACK_BOTTOM_UP");
+    cbvh::set_treelet_packing((int)value);
     return CBVH_OK;
   }
   return cbvh::fail(CBVH_ERR_ARG, "unknown option");

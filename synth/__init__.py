@@ -15,6 +15,7 @@ translation t, and maps a point of mesh B into the frame of mesh A: x_A = R x_B 
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -22,7 +23,7 @@ import numpy as np
 __all__ = [
     "icosphere", "heightfield", "ValueNoise2D", "box_mesh", "capsule", "shoemake_rotations",
     "poses_box", "poses_terrain", "dh_link_poses", "merge_meshes", "transform_mesh",
-    "scene_diameter", "C1", "C2", "C3", "clutter", "arm_links",
+    "scene_diameter", "C1", "C2", "C3", "C5", "clutter", "arm_links",
 ]
 
 _PHI = (1.0 + math.sqrt(5.0)) / 2.0
@@ -39,8 +40,21 @@ _ICO_F = np.array([
 ], dtype=np.int64)
 
 
+@functools.lru_cache(maxsize=8)
+def _unit_icosphere_cached(level: int):
+    v, f = _unit_icosphere_build(level)
+    v.setflags(write=False)
+    f.setflags(write=False)
+    return v, f
+
+
 def _unit_icosphere(level: int):
     """Unit icosphere: the icosahedron with each face split into 4, `level` times."""
+    v, f = _unit_icosphere_cached(level)
+    return v.copy(), f.copy()
+
+
+def _unit_icosphere_build(level: int):
     v = list(_ICO_V / np.linalg.norm(_ICO_V, axis=1, keepdims=True))
     f = _ICO_F.copy()
     for _ in range(level):
@@ -383,3 +397,23 @@ def C3(n_configs: int = 200000, n_boxes: int = 200, n_spheres: int = 200):
     rng = np.random.default_rng(2003)
     q = rng.uniform(-np.pi, np.pi, size=(n_configs, 6))
     return dict(A=A, links=links, link_poses=dh_link_poses(q), q=q, k=24, m=8, bits=8, treelet=16384)
+
+
+def C5(n_poses: int = 1_000_000, n_spheres: int = 32, level: int = 7, probe_level: int = 6,
+       half: float = 10.0):
+    """Scale workload: an environment of `n_spheres` fractal-displaced level-`level` icospheres
+    (radius U(0.5, 2), 4-octave noise, amplitude 0.15, uniform rotation) with centres uniform in
+    [-half, half]^3 -- 32 level-7 spheres make 10,485,760 triangles -- probed by a displaced
+    level-6 icosphere (81,920 triangles, radius 1) at poses with uniform rotation and translation
+    uniform in the cube.  Seeds 1005 (environment), 1015 (probe), 2005 (poses)."""
+    rng = np.random.default_rng(1005)
+    parts = []
+    for k in range(n_spheres):
+        r = rng.uniform(0.5, 2.0)
+        v, t = icosphere(level, r, 0.15, seed=1005 * 7 + k, fractal=True)
+        R = shoemake_rotations(rng, 1)[0]
+        parts.append((transform_mesh(v, R, rng.uniform(-half, half, size=3)), t))
+    A = merge_meshes(parts)
+    B = icosphere(probe_level, 1.0, 0.15, seed=1015)
+    P = poses_box(n_poses, seed=2005, lo=-half, hi=half)
+    return dict(A=A, B=B, poses=P, k=18, m=4, bits=8, treelet=16384)

@@ -40,10 +40,17 @@ CONFIGS = [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096), (26, 16, 16, 8
            (24, 8, 16, 65536), (18, 2, 16, 131072), (18, 16, 8, 32768)]
 
 
+@pytest.fixture(params=[0, 1], ids=["top_down", "bottom_up"])
+def packing(cb, request):
+    cb.set_option(cb.OPT_TREELET_PACKING, request.param)
+    yield request.param
+    cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
+
+
 @pytest.mark.parametrize("k,m,bits,tb", CONFIGS)
-def test_blob_identical_to_oracle(cb, k, m, bits, tb):
+def test_blob_identical_to_oracle(cb, packing, k, m, bits, tb):
     v, t = synth.icosphere(3, 1.0, 0.15, seed=k + m + bits)
-    o = oracle.BVH(v, t, k, m, bits, tb)
+    o = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
     h = cb.BVH(v, t, k, m, bits, tb, device=None)
     assert h.info["n_nodes"] == o.n_nodes and h.info["n_treelets"] == o.n_treelets
     assert h.info["lattice_exp"] == o.e and h.info["depth"] == o.depth
@@ -51,14 +58,14 @@ def test_blob_identical_to_oracle(cb, k, m, bits, tb):
     assert len(bo) == len(bl) and (bo == bl).all()
 
 
-def test_blob_identical_to_oracle_terrain_and_odd_meshes(cb):
+def test_blob_identical_to_oracle_terrain_and_odd_meshes(cb, packing):
     va, ta, _ = synth.heightfield(96, seed=31)
     for v, t in [(va, ta), synth.box_mesh((1.0, 2.0, 3.0)), synth.capsule(0.5, 0.1, 2000, seed=3),
                  (np.array([[0, 0, 0], [1e-3, 0, 0], [0, 2e-3, 1e-4]], np.float32), np.array([[0, 1, 2]], np.int32)),
                  (np.array([[1e6, 1e6, 1e6], [1e6 + 64, 1e6, 1e6], [1e6, 1e6 + 64, 1e6 - 32]], np.float32),
                   np.array([[0, 1, 2]], np.int32))]:
         for k, m, bits, tb in [(24, 8, 8, 16384), (18, 4, 16, 4096)]:
-            o = oracle.BVH(v, t, k, m, bits, tb)
+            o = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
             h = cb.BVH(v, t, k, m, bits, tb, device=None)
             assert (o.blob() == h.blob_host()).all()
 
@@ -118,3 +125,4 @@ def test_batch_rejects_unattached_handles(cb):
     assert cb.lib.cbvh_batch_create(q, 1, C.byref(h)) == -9
     assert cb.lib.cbvh_set_option(99, 0) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_STAGE_BYTES, 1 << 20) == -1
+    assert cb.lib.cbvh_set_option(cb.OPT_TREELET_PACKING, 2) == -1

@@ -147,11 +147,12 @@ def test_tree_split_properties(m):
         check_split([sets[tr["first"][x] + c] for c in range(nc)])
 
 
+@pytest.mark.parametrize("packing", [oracle.PACKING_TOP_DOWN, oracle.PACKING_BOTTOM_UP])
 @pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
                                          (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536)])
-def test_encoding_invariants(k, m, bits, tb):
+def test_encoding_invariants(k, m, bits, tb, packing):
     v, t = synth.icosphere(3, 1.0, 0.15, seed=5)
-    h = oracle.BVH(v, t, k, m, bits, tb)
+    h = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
     tr = h.tree()
     L = h.lattice()
     ex, dec, decf = L["exact"], L["decoded"], L["decf"]
@@ -180,6 +181,27 @@ def test_encoding_invariants(k, m, bits, tb):
         assert (lat == dec[order]).all()
     assert (f.view(np.uint32) == decf[order].view(np.uint32)).all()
     assert ((meta[:, 0] >> 16) & 31 == tr["nchild"][order]).all()
+    # treelets hold whole sibling groups: a node and its siblings share a treelet, and a
+    # non-root node's parent is in the same treelet
+    par_all = tr["parent"]
+    nonroot = ~roots
+    assert (pl["treelet"][nonroot] == pl["treelet"][par_all[nonroot]]).all()
+    fit = (tb - 16 - h.root_bytes) // h.rec_bytes + 1
+    if packing == oracle.PACKING_BOTTOM_UP:
+        # bottom-up rule, checked against its statement: an inner node's children were cut
+        # off exactly when the node plus the nodes of their treelets would not fit one treelet
+        for x in range(h.n_nodes):
+            nc = tr["nchild"][x]
+            if nc == 0:
+                continue
+            kids = tr["first"][x] + np.arange(nc)
+            cut = pl["treelet"][kids[0]] != pl["treelet"][x]
+            assert (pl["treelet"][kids] != pl["treelet"][x]).all() == cut
+            if cut:
+                assert 1 + counts[pl["treelet"][kids]].sum() > fit
+        # treelets are numbered in node order of their roots
+        rn = np.flatnonzero(roots)
+        assert (pl["treelet"][rn] == np.arange(len(rn))).all()
 
 
 def test_bad_arguments_and_meshes():
