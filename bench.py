@@ -229,28 +229,21 @@ def arm_sweep(cb, torch, dev, n_configs):
             "plain": "one cbvh_collide per link, one warp per pose"}
 
 
-def serving(cb, torch, dev, models, rates=(100, 300, 1000), seconds=1.0, seed=2004):
-    """Request loop under open-loop Poisson arrivals: requests of log-uniform 1..4096 poses,
-    CD:PQ 1:1, robots (arm link, level-5 and level-3 spheres) against the terrain and the
-    clutter.  Reports p50/p99 latency and throughput; the plain form serves the same requests
-    one call at a time in arrival order."""
+def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 10000, 50000), max_requests=400,
+            seed=2004):
+    """Request loop under open-loop Poisson arrivals (the serving workload: terrain and clutter
+    environments; the 6-link arm and the level-5 and level-3 spheres as robots; collision and
+    distance 1:1; log-uniform 1..4096 configurations per request).  Each offered rate runs
+    for min(2 s, max_requests / rate) of arrivals.  Reports p50/p99 latency and throughput;
+    the plain form serves the same requests one call per model pair (per link for the arm),
+    in arrival order."""
     from paper_2012_05348_gb300.serve import Server
     import threading
-    rng = np.random.default_rng(seed)
-    envs, robots = ["terrain", "clutter"], ["link", "sphere5", "sphere3"]
     out = []
     for rate in rates:
-        n_req = max(1, int(rate * seconds))
-        gaps = rng.exponential(1.0 / rate, size=n_req)
-        reqs = []
-        for i in range(n_req):
-            n = int(np.exp(rng.uniform(0, np.log(4096))))
-            env, rob = envs[i % 2], robots[i % 3]
-            P = synth.poses_box(n, seed=int(rng.integers(1 << 30)), lo=-1.5, hi=1.5)
-            if env == "terrain":
-                P[:, 11] = np.abs(P[:, 11]) * 0.3 + 0.5
-            reqs.append((env, rob, "collide" if i % 2 == 0 else "distance", P))
-        srv = Server(models, mem_budget=8 << 30, device=dev)
+        secs = min(2.0, max_requests / rate)
+        gaps, reqs = synth.C4(rate, secs, height_fn, seed=seed + int(rate))
+        srv = Server(models, mem_budget=8 << 30, device=dev, robots=robots)
         futs = []
 
         def gen():
@@ -261,30 +254,38 @@ def serving(cb, torch, dev, models, rates=(100, 300, 1000), seconds=1.0, seed=20
                 d = t0 + t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                futs.append(srv.submit(env, rob, kind, P, early_exit=False))
+                futs.append(srv.submit(env, rob, kind, P))
         t_start = time.perf_counter()
         th = threading.Thread(target=gen)
         th.start()
         th.join()
         for f in futs:
-            f.result(timeout=600)
+            f.result(timeout=900)
         t_end = time.perf_counter()
         srv.close()
         st = srv.stats()
-        poses = sum(len(r[3]) for r in reqs)
-        # plain: the same requests, one call at a time
+        configs = sum(len(r[3]) for r in reqs)
+        link_poses = sum(len(r[3]) * (6 if r[1] == "arm" else 1) for r in reqs)
+        # plain: the same requests, one call per model pair, results back on the host
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for env, rob, kind, P in reqs:
-            Pd = torch.as_tensor(P, device=dev)
-            if kind == "collide":
-                cb.collide(models[env], models[rob], Pd, pairs=False).hit.cpu()
-            else:
-                cb.distance(models[env], models[rob], Pd).cpu()
+            names = robots.get(rob, [rob])
+            res = []
+            for i, name in enumerate(names):
+                Pd = torch.as_tensor(np.ascontiguousarray(P[:, i] if len(names) > 1 else P), device=dev)
+                if kind == "collide":
+                    res.append(cb.collide(models[env], models[name], Pd, pairs=False).hit.cpu())
+                else:
+                    res.append(cb.distance(models[env], models[name], Pd).cpu())
         t_plain = time.perf_counter() - t0
-        out.append({"rate_req_per_s": rate, "requests": n_req, "poses": poses, "batches": st["batches"],
+        out.append({"offered_req_per_s": rate, "arrival_window_s": secs, "requests": len(reqs),
+                    "configurations": configs, "link_poses": link_poses, "batches": st["batches"],
                     "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                    "served_poses_per_s": poses / (t_end - t_start), "plain_poses_per_s": poses / t_plain})
+                    "served_req_per_s": len(reqs) / (t_end - t_start),
+                    "served_configs_per_s": configs / (t_end - t_start),
+                    "plain_configs_per_s": configs / t_plain,
+                    "speedup_vs_plain": t_plain / (t_end - t_start)})
     return out
 
 
@@ -439,10 +440,12 @@ def main():
     if not args.no_extra:
         extra["batched"] = arm_sweep(cb, torch, dev, args.arm_configs)
         c3 = synth.C3(8)
-        models = {"terrain": A, "clutter": cb.BVH(*c3["A"], 24, 8, 8, 16384, device=dev),
-                  "link": cb.BVH(*c3["links"][3], 24, 8, 8, 16384, device=dev), "sphere5": B,
+        models = {"terrain": A, "clutter": cb.BVH(*c3["A"], 24, 8, 8, 16384, device=dev), "sphere5": B,
                   "sphere3": cb.BVH(*synth.C1(1)["B"], 24, 8, 8, 16384, device=dev)}
-        extra["served"] = serving(cb, torch, dev, models)
+        for i, link in enumerate(c3["links"]):
+            models[f"link{i}"] = cb.BVH(*link, 24, 8, 8, 16384, device=dev)
+        robots = {"arm": [f"link{i}" for i in range(6)]}
+        extra["served"] = serving(cb, torch, dev, models, robots, c["height"])
     cpu = None
     if not args.no_cpu_baseline:
         rate, done, secs, cores = oracle_rate(c, args.cpu_sample)

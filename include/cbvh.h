@@ -42,7 +42,8 @@ extern "C" {
 #define CBVH_ERR_STATE (-9)     /* handle has no device blob attached */
 
 /* collide flags */
-#define CBVH_EARLY_EXIT 1u /* stop each pose at its first intersecting pair (pair outputs must be NULL) */
+#define CBVH_EARLY_EXIT 1u /* stop each pose at its first intersecting pair (pair outputs must be NULL);
+                            * implied whenever no pair outputs are requested */
 #define CBVH_SORT_PAIRS 2u /* sort each pose's pair list by (i, j) */
 
 typedef struct cbvh_bvh cbvh_bvh; /* opaque; immutable once built; concurrent reads are safe */
@@ -150,7 +151,8 @@ int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const float *pos
 
 /* ---- batched queries (one pass of persistent launches over many work items) ----
  * A work item pairs a static hierarchy A with a posed hierarchy B for n poses and asks for
- * collision flags (mode 0; flags CBVH_EARLY_EXIT or 0) or distances (mode 1).  Items that
+ * collision flags (mode 0; flags CBVH_EARLY_EXIT or 0, which act the same: with flags only,
+ * every pose stops at its first intersecting pair) or distances (mode 1).  Items that
  * share the query kind and A's k run in one set of persistent launches, so items of very
  * different sizes (robot links against a scene, many requests) share the GPU.  Outputs and
  * semantics per item are those of cbvh_collide without pairs and of cbvh_distance. */

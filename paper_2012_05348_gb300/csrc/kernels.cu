@@ -67,7 +67,7 @@ struct Layout {
   int st_off[2], st_bytes[2], st_cnt[2], st_toff[2], o_bar;
   int warp_bytes;
   int o_stack, stack_cap;
-  int o_leafq, leafq_cap;
+  int o_leafq, o_leafqlb, leafq_cap;
   int o_pose;
   int o_tagA, o_latA, o_pathA;
   int o_tagB, o_latB, o_pathB;
@@ -610,8 +610,12 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
   const int wib = threadIdx.x >> 5;
   const bool staged = BATCH ? false : stage_treelets(p, smem);
   uint8_t *ws = smem + p.L.cta_bytes + wib * p.L.warp_bytes;
-  uint2 *stack = p.stacks + ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) * (size_t)p.L.stack_cap;
+  uint2 *stack = reinterpret_cast<uint2 *>(reinterpret_cast<uint8_t *>(p.stacks) +
+                                           ((size_t)blockIdx.x * (blockDim.x >> 5) + wib) *
+                                               (size_t)((p.L.stack_cap * 12 + 15) & ~15));
+  float *stack_lb = reinterpret_cast<float *>(stack + p.L.stack_cap);  // PQ: lower bound of each entry
   uint2 *leafq = reinterpret_cast<uint2 *>(ws + p.L.o_leafq);
+  float *leafq_lb = reinterpret_cast<float *>(ws + p.L.o_leafqlb);
   float *pc = reinterpret_cast<float *>(ws + p.L.o_pose);
   constexpr int KS = (KA & 1) ? KA : KA + 1;
   Side SA{reinterpret_cast<uint32_t *>(ws + p.L.o_tagA),
@@ -671,6 +675,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
     if (task >= n_in) break;
     uint32_t gid, a, b;  // global pose id (equal to the pose index of a single query)
     bool root;
+    float task_lb = 0.f;  // PQ: lower bound of the task's node pair
     if (p.round == 0) {
       gid = task;
       a = b = 0;
@@ -680,6 +685,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
       gid = t.x;
       a = t.y;
       b = t.z;
+      task_lb = __uint_as_float(t.w);
       root = false;
     }
     if (BATCH) {
@@ -759,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
       float v = 0.f;
       if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
       best = __shfl_sync(kFull, v, 0);
+      if (task_lb >= best) continue;  // a closer pair was found after this one was handed on
     } else if (early) {
       int h = 0;
       if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
@@ -773,11 +780,13 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
     // checkPrimitives on the last `cnt` queued leaf pairs, one pair per lane
     auto drain = [&](int cnt) {
       nleaf -= cnt;
-      n_leaf += cnt;
       bool h = false;
       float dl = INFINITY;
       uint32_t ia = 0, ib = 0;
-      if (lane < cnt) {
+      // PQ: a queued pair whose bound reached the best distance found since is skipped
+      const bool test = lane < cnt && (MODE == MODE_CD || leafq_lb[nleaf + lane] < best);
+      n_leaf += __popc(__ballot_sync(kFull, test));
+      if (test) {
         const uint2 e = leafq[nleaf + lane];
         V3 P[3], Q[3];
         load_pair(A.tris, B.tris, pc, e.x, e.y, P, Q, ia, ib);
@@ -893,8 +902,14 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
           break;
         }
         const int pos = sp + __popc(mi & lt);
-        if (isleaf) leafq[nleaf + __popc(ml & lt)] = make_uint2(aleaf[i], bleaf[j]);
-        if (keep && !isleaf) stack[pos] = make_uint2(aref[i], bref[j]);
+        if (isleaf) {
+          leafq[nleaf + __popc(ml & lt)] = make_uint2(aleaf[i], bleaf[j]);
+          if (MODE == MODE_PQ) leafq_lb[nleaf + __popc(ml & lt)] = lb;
+        }
+        if (keep && !isleaf) {
+          stack[pos] = make_uint2(aref[i], bref[j]);
+          if (MODE == MODE_PQ) stack_lb[pos] = lb;
+        }
         if (MODE == MODE_PQ && mi) {
           float mv = (keep && !isleaf) ? lb : INFINITY;
           int mp = pos;
@@ -925,6 +940,9 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
           const uint2 x = stack[run_pos];
           stack[run_pos] = stack[sp - 1];
           stack[sp - 1] = x;
+          const float xl = stack_lb[run_pos];
+          stack_lb[run_pos] = stack_lb[sp - 1];
+          stack_lb[sp - 1] = xl;
         }
         __syncwarp();
       }
@@ -951,7 +969,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
         if (ok) {
           for (int k = lane; k < sp; k += 32) {
             const uint2 e = stack[k];
-            p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, 0u);
+            p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, MODE == MODE_PQ ? __float_as_uint(stack_lb[k]) : 0u);
           }
           sp = 0;
           __syncwarp();
@@ -970,6 +988,12 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(con
         }
       }
       // ---------------- pop ----------------
+      // PQ: entries whose lower bound reached the best distance found since they were
+      // pushed cannot hold a closer pair and are dropped
+      if (MODE == MODE_PQ) {
+        while (sp > 0 && stack_lb[sp - 1] >= best) --sp;
+        if (sp == 0) break;
+      }
       const uint2 e = stack[--sp];
       a = e.x;
       b = e.y;
@@ -1189,6 +1213,8 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   L.o_stack = -1;  // stacks live in global memory
   L.o_leafq = o;
   o = align16(o + 8 * L.leafq_cap);
+  L.o_leafqlb = o;
+  o = align16(o + 4 * L.leafq_cap);
   L.o_pose = o;
   o = align16(o + 4 * (12 + kPoseJ * KA));
   L.o_tagA = o;
@@ -1212,6 +1238,10 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   L.warp_bytes = o;
   return L;
 }
+
+// Bytes of one warp's node-pair stack: stack_cap (A node, B node) entries, then the lower
+// bound of each entry (read by the proximity query when it pops or hands on an entry).
+int64_t stack_stride(int stack_cap) { return ((int64_t)stack_cap * 12 + 15) & ~int64_t(15); }
 
 // Stack bound: every level of the node-pair tree leaves at most (mA mB - 1) siblings.
 int stack_bound(const cbvh_bvh *A, const cbvh_bvh *B) { return 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1); }
@@ -1298,7 +1328,7 @@ WsPlan ws_plan(const Layout &L, int64_t n, int mode, int64_t cap, int sms) {
   o = align256(o + 16 * tcap);
   w.warps_max = sms * kMaxWarpsPerSM;
   w.stacks = o;
-  o = align256(o + (int64_t)w.warps_max * L.stack_cap * 8);
+  o = align256(o + (int64_t)w.warps_max * stack_stride(L.stack_cap));
   w.total = o;
   return w;
 }
@@ -1473,6 +1503,8 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
     }
     return CBVH_OK;
   }
+  // only the flags are asked for: each pose can stop at its first intersecting pair
+  if (!want_pairs) flags |= CBVH_EARLY_EXIT;
   p.poses = poses;
   p.n = n;
   p.hit = hit;
@@ -1635,7 +1667,7 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
   // carve the fixed array: counters, two task buffers, then as many warp stacks as fit
   const int64_t tasks_bytes = 16 * (int64_t)kNoAllocTasks;
   const int64_t stacks_off = kWsHeader + 2 * tasks_bytes;
-  const int64_t per_warp = 8 * (int64_t)p.L.stack_cap;
+  const int64_t per_warp = stack_stride(p.L.stack_cap);
   const int64_t warps_fit = ((int64_t)kNoAllocScratchBytes - stacks_off) / per_warp;
   if (warps_fit < kWarpsPerBlock)
     return cbvh::fail(CBVH_ERR_WORKSPACE,
@@ -1748,7 +1780,7 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
         it.poses = x.poses;
         it.hit = x.hit;
         it.dist = x.dist;
-        it.flags = x.flags;
+        it.flags = x.mode == 0 ? (x.flags | CBVH_EARLY_EXIT) : 0;  // collision items return flags only
         b->items.push_back(it);
         b->bases.push_back(acc);
         acc += (unsigned long long)x.n;
@@ -1800,7 +1832,7 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
   b->o_tasks1 = o;
   o = align256(o + 16 * tcap);
   b->o_stacks = o;
-  o = align256(o + (int64_t)b->sms * kMaxWarpsPerSM * max_stack * 8);
+  o = align256(o + (int64_t)b->sms * kMaxWarpsPerSM * stack_stride(max_stack));
   b->total = o;
   (void)total_poses;
   *out = b;

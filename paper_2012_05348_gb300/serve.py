@@ -8,6 +8,10 @@ others are on the GPU join the next batch, each batch runs as one set of persist
 Admission is by a device-memory budget: a batch takes requests in arrival order while the
 memory it needs (poses, outputs, workspace) fits in what the budget has left.  Per-request
 latency (submit to result) is recorded for p50 / p99.
+
+A robot is either one hierarchy or a chain of links (``robots``: name -> link model names);
+a request for a chain carries one pose per link and configuration, runs as one batch item
+per link, and resolves to "any link collides" or "smallest distance over the links".
 """
 from __future__ import annotations
 
@@ -32,19 +36,21 @@ class Request:
 
 
 class Server:
-    """models: name -> attached BVH.  mem_budget: device bytes that batches in flight may use.
-    max_poses: cap on the poses of one batch."""
+    """models: name -> attached BVH.  robots: name -> list of link model names (chains such as
+    an arm); a plain model name also serves as a robot.  mem_budget: device bytes that batches
+    in flight may use.  max_poses: cap on the link poses of one batch."""
 
     def __init__(self, models: dict, mem_budget: int = 1 << 30, slots: int = 2, max_poses: int = 1 << 16,
-                 device="cuda"):
+                 device="cuda", robots: dict | None = None):
         torch = _torch()
         self.models = models
+        self.robots = dict(robots or {})
         self.mem_budget = int(mem_budget)
         self.max_poses = int(max_poses)
         dev = torch.device(device)
         self.device = torch.device("cuda", dev.index if dev.index is not None else torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
-        self.busy = [None] * slots  # per slot: (event, requests, host outputs, bytes)
+        self.busy = [None] * slots  # per slot: (event, requests, host outputs, bytes, batch)
         self.used = 0
         self.pending = collections.deque()
         self.cv = threading.Condition()
@@ -56,14 +62,24 @@ class Server:
         self.thread.start()
 
     # ---------------------------------------------------------------- client side
+    def links(self, robot: str) -> list:
+        return list(self.robots[robot]) if robot in self.robots else [robot]
+
     def submit(self, env: str, robot: str, kind: str, poses: np.ndarray, early_exit: bool = False) -> Future:
         """Queue a request; the future resolves to uint8 hit flags ('collide') or float32
-        distances ('distance'), one per pose."""
+        distances ('distance'), one per configuration.  poses: (n, 12) for a single model,
+        (n, L, 12) for a chain of L links.  Collision requests return flags only, so every
+        configuration stops at its first intersecting pair whatever ``early_exit`` says."""
         if kind not in ("collide", "distance"):
             raise ValueError("kind must be 'collide' or 'distance'")
-        if env not in self.models or robot not in self.models:
+        if env not in self.models:
             raise KeyError("unknown model")
-        poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 12)
+        links = self.links(robot)
+        if any(l not in self.models for l in links):
+            raise KeyError("unknown model")
+        L = len(links)
+        poses = np.ascontiguousarray(poses, dtype=np.float32)
+        poses = poses.reshape(-1, L, 12) if L > 1 else poses.reshape(-1, 12)
         r = Request(env, robot, kind, poses, early_exit)
         with self.cv:
             if not self.running:
@@ -89,18 +105,29 @@ class Server:
         # poses + outputs + the batch workspace's per-pose share (task buffers) + a fixed part
         return n_poses * (48 + 4 + 1 + 2 * 16 * 256) + (96 << 20)
 
+    @staticmethod
+    def _link_poses(r) -> int:
+        return r.poses.shape[0] * (r.poses.shape[1] if r.poses.ndim == 3 else 1)
+
     def _complete(self, slot):
         ev, reqs, outs, nbytes, batch = self.busy[slot]
         ev.synchronize()
         code = int(batch.status.item())
         now = time.perf_counter()
-        for r, o in zip(reqs, outs):
+        for r, parts in zip(reqs, outs):
             r.t_done = now
             self.latencies.append(now - r.t_submit)
             if code != 0:
                 r.future.set_exception(CbvhError(code, "device status"))
+                continue
+            vals = [o.numpy() for o in parts]
+            if len(vals) == 1:
+                res = vals[0].copy()
+            elif r.kind == "collide":
+                res = np.maximum.reduce(vals)
             else:
-                r.future.set_result(o.numpy().copy())
+                res = np.minimum.reduce(vals)
+            r.future.set_result(res)
         self.busy[slot] = None
         self.used -= nbytes
 
@@ -109,7 +136,7 @@ class Server:
         take, n, need = [], 0, 0
         while self.pending:
             r = self.pending[0]
-            rn = len(r.poses)
+            rn = self._link_poses(r)
             b = self._bytes(n + rn)
             if take and (n + rn > self.max_poses or self.used + b > self.mem_budget):
                 break
@@ -124,26 +151,37 @@ class Server:
         torch = _torch()
         stream = self.streams[slot]
         with torch.cuda.stream(stream):
-            n_total = sum(len(r.poses) for r in reqs)
+            # one part per (request, link): its poses are contiguous in one pinned buffer
+            parts = []
+            for r in reqs:
+                links = self.links(r.robot)
+                for i, name in enumerate(links):
+                    parts.append((r, name, r.poses[:, i] if len(links) > 1 else r.poses))
+            n_total = sum(len(P) for _, _, P in parts)
             host = torch.empty((max(1, n_total), 12), dtype=torch.float32, pin_memory=True)
             o = 0
-            for r in reqs:
-                host[o:o + len(r.poses)] = torch.from_numpy(r.poses)
-                o += len(r.poses)
+            for _, _, P in parts:
+                host[o:o + len(P)] = torch.from_numpy(np.ascontiguousarray(P))
+                o += len(P)
             dev = host.to(self.device, non_blocking=True)
             items, o = [], 0
-            for r in reqs:
-                n = len(r.poses)
-                items.append(dict(A=self.models[r.env], B=self.models[r.robot], kind=r.kind,
+            for r, name, P in parts:
+                n = len(P)
+                items.append(dict(A=self.models[r.env], B=self.models[name], kind=r.kind,
                                   poses=dev[o:o + n], early_exit=r.early_exit))
                 o += n
             batch = Batch(items, device=self.device)
             batch.launch(stream)
-            outs = []
-            for out in batch.outputs:
-                h = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
-                h.copy_(out, non_blocking=True)
-                outs.append(h)
+            outs, k = [], 0
+            for r in reqs:
+                mine = []
+                for _ in self.links(r.robot):
+                    out = batch.outputs[k]
+                    h = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+                    h.copy_(out, non_blocking=True)
+                    mine.append(h)
+                    k += 1
+                outs.append(mine)
             ev = torch.cuda.Event()
             ev.record(stream)
         self.busy[slot] = (ev, reqs, outs, nbytes, batch)

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "icosphere", "heightfield", "ValueNoise2D", "box_mesh", "capsule", "shoemake_rotations",
     "poses_box", "poses_terrain", "dh_link_poses", "merge_meshes", "transform_mesh",
-    "scene_diameter", "C1", "C2", "C3", "C5", "clutter", "arm_links",
+    "scene_diameter", "C1", "C2", "C3", "C4", "C5", "clutter", "arm_links",
 ]
 
 _PHI = (1.0 + math.sqrt(5.0)) / 2.0
@@ -417,3 +417,39 @@ def C5(n_poses: int = 1_000_000, n_spheres: int = 32, level: int = 7, probe_leve
     B = icosphere(probe_level, 1.0, 0.15, seed=1015)
     P = poses_box(n_poses, seed=2005, lo=-half, hi=half)
     return dict(A=A, B=B, poses=P, k=18, m=4, bits=8, treelet=16384)
+
+
+def C4(rate: float, seconds: float, height_fn, seed: int = 2004, max_poses: int = 4096):
+    """Serving workload: open-loop Poisson arrivals at ``rate`` requests/s for ``seconds``.
+    Each request independently draws an environment (terrain or clutter), a robot (the 6-link
+    arm, the level-5 sphere or the level-3 sphere), a kind (collision or distance, 1:1) and a
+    size log-uniform in [1, max_poses] configurations.  Poses follow the workloads the models
+    come from: spheres over the terrain as in the terrain workload (``height_fn``), spheres in
+    the clutter uniform in its 4 m cube, the arm in the clutter at the origin with joint
+    angles U[-pi, pi]^6, the arm on the terrain with its base 0.2 above a uniform point of the
+    footprint.  Returns (gaps (s), requests [(env, robot, kind, poses)]); arm poses are
+    (n, 6, 12), sphere poses (n, 12)."""
+    rng = np.random.default_rng(seed)
+    n_req = max(1, int(round(rate * seconds)))
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    reqs = []
+    for _ in range(n_req):
+        env = ("terrain", "clutter")[int(rng.integers(2))]
+        robot = ("arm", "sphere5", "sphere3")[int(rng.integers(3))]
+        kind = ("collide", "distance")[int(rng.integers(2))]
+        n = min(max_poses, int(math.ceil(math.exp(rng.uniform(0.0, math.log(max_poses))))))
+        sub = int(rng.integers(1 << 30))
+        if robot == "arm":
+            r2 = np.random.default_rng(sub)
+            P = dh_link_poses(r2.uniform(-np.pi, np.pi, size=(n, 6)))
+            if env == "terrain":
+                xy = r2.uniform(-2.0, 2.0, size=(n, 2))
+                base = np.concatenate([xy, (height_fn(xy[:, 0], xy[:, 1]) + 0.2)[:, None]], axis=1)
+                P = P.copy()
+                P[:, :, 9:] = (P[:, :, 9:].astype(np.float64) + base[:, None, :]).astype(np.float32)
+        elif env == "terrain":
+            P = poses_terrain(n, seed=sub, height_fn=height_fn)
+        else:
+            P = poses_box(n, seed=sub, lo=-2.0, hi=2.0)
+        reqs.append((env, robot, kind, P))
+    return gaps, reqs

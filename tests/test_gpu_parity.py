@@ -52,11 +52,23 @@ def _filtered(Ao, Bo, draw, n, D):
 
 
 # ------------------------------------------------------------------ decode
+@pytest.fixture
+def bottom_up(cb):
+    cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_BOTTOM_UP)
+    yield
+    cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
+
+
+@pytest.mark.parametrize("packing", [0, 1])
 @pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
                                          (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536)])
-def test_decode_bit_exact(cb, k, m, bits, tb):
+def test_decode_bit_exact(cb, k, m, bits, tb, packing):
     v, t = synth.icosphere(4, 1.0, 0.15, seed=40 + k)
-    h = cb.BVH(v, t, k, m, bits, tb)
+    cb.set_option(cb.OPT_TREELET_PACKING, packing)
+    try:
+        h = cb.BVH(v, t, k, m, bits, tb)
+    finally:
+        cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
     lat, f = h.decode_all()
     o_lat, o_f, _ = oracle.decode_blob(h.blob_host())
     assert (f.cpu().numpy().view(np.uint32) == o_f.view(np.uint32)).all()
@@ -130,6 +142,19 @@ def test_other_configs_bit_exact(cb, c1, k, m, bits, tb):
     A = cb.BVH(va, ta, k, m, bits, tb)
     B = cb.BVH(vb, tb_, k, m, bits, tb)
     P = c1["P"][:96]
+    o_hit, o_off, o_ij, _ = oracle.collide(c1["Ao"], c1["Bo"], P)
+    _check_cd(cb.collide(A, B, _gpu(P)), o_hit, o_off, o_ij)
+    o_d, _ = oracle.distance(c1["Ao"], c1["Bo"], P)
+    d = cb.distance(A, B, _gpu(P)).cpu().numpy()
+    assert np.abs(d - o_d).max() <= TOL_PQ * c1["D"]
+
+
+@pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (18, 4, 8, 131072), (18, 4, 0, 16384)])
+def test_bottom_up_packing_bit_exact(cb, c1, bottom_up, k, m, bits, tb):
+    va, ta, vb, tb_ = c1["mesh"]
+    A = cb.BVH(va, ta, k, m, bits, tb)
+    B = cb.BVH(vb, tb_, k, m, bits, tb)
+    P = c1["P"][:128]
     o_hit, o_off, o_ij, _ = oracle.collide(c1["Ao"], c1["Bo"], P)
     _check_cd(cb.collide(A, B, _gpu(P)), o_hit, o_off, o_ij)
     o_d, _ = oracle.distance(c1["Ao"], c1["Bo"], P)
@@ -307,3 +332,20 @@ def test_launch_options_keep_results(cb, c1, c2, stage, split, budget0):
         assert torch.equal(r.hit, g.hit) and torch.equal(r.offsets, g.offsets) and torch.equal(r.pairs, g.pairs)
     assert np.allclose(ref[1], got[1], rtol=0, atol=1e-5 * c1["D"])
     assert np.allclose(ref[3], got[3], rtol=0, atol=1e-5 * c2["D"])
+
+
+def test_bottom_up_terrain_equals_top_down(cb, c2):
+    """The two treelet packings give different blobs of the same tree: every collision
+    result is identical and distances agree to rounding."""
+    import torch
+    cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_BOTTOM_UP)
+    try:
+        A = cb.BVH(*c2["c"]["A"], 24, 8, 8, 16384)
+    finally:
+        cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
+    assert A.info["node_bytes"] < c2["A"].info["node_bytes"]
+    P = _gpu(c2["c"]["poses"][:2000])
+    r0, r1 = cb.collide(c2["A"], c2["B"], P), cb.collide(A, c2["B"], P)
+    assert torch.equal(r0.hit, r1.hit) and torch.equal(r0.offsets, r1.offsets) and torch.equal(r0.pairs, r1.pairs)
+    d0, d1 = cb.distance(c2["A"], c2["B"], P).cpu().numpy(), cb.distance(A, c2["B"], P).cpu().numpy()
+    assert np.abs(d0 - d1).max() <= 1e-6 * c2["D"]

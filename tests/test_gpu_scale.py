@@ -1,0 +1,62 @@
+"""The scale-and-compression workload: a field of fractal-displaced spheres probed by a
+displaced sphere, with bottom-up packed treelets at 8 and 16 bits and with FP32 bounds.
+
+- A reduced field (6 level-4 spheres in a 6 m cube, level-3 probe) against the FP64 oracle
+  in full: collision bit-exact on poses away from contact, distances within 1e-5 of the
+  scene diameter, for every compression setting.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_PQ = 1e-5
+EPS_NEAR = 1e-6
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_05348_gb300 import _build
+    _build.build()
+    import paper_2012_05348_gb300 as m
+    m.set_option(m.OPT_TREELET_PACKING, m.PACK_BOTTOM_UP)
+    yield m
+    m.set_option(m.OPT_TREELET_PACKING, m.PACK_TOP_DOWN)
+
+
+@pytest.fixture(scope="module")
+def field(cb):
+    c = synth.C5(1, n_spheres=6, level=4, probe_level=3, half=3.0)
+    (va, ta), (vb, tb) = c["A"], c["B"]
+    Ao = oracle.BVH(va, ta, 18, 4, 8, 16384, packing=oracle.PACKING_BOTTOM_UP)
+    Bo = oracle.BVH(vb, tb, 18, 4, 8, 16384, packing=oracle.PACKING_BOTTOM_UP)
+    D = synth.scene_diameter(va, vb)
+    P = oracle.filtered_poses(Ao, Bo, lambda cnt, r: synth.poses_box(cnt, seed=2005 + 7919 * r, lo=-3.0, hi=3.0),
+                              384, EPS_NEAR * D)
+    return dict(mesh=(va, ta, vb, tb), Ao=Ao, Bo=Bo, D=D, P=P)
+
+
+@pytest.mark.parametrize("bits,tb", [(8, 16384), (16, 16384), (0, 16384), (8, 131072), (16, 65536)])
+def test_reduced_field_against_oracle(cb, field, bits, tb):
+    import torch
+    va, ta, vb, tb_ = field["mesh"]
+    A = cb.BVH(va, ta, 18, 4, bits, tb)
+    B = cb.BVH(vb, tb_, 18, 4, bits, tb)
+    P = field["P"]
+    Pd = torch.as_tensor(P, device="cuda")
+    o_hit, o_off, o_ij, _ = oracle.collide(field["Ao"], field["Bo"], P)
+    assert o_hit.sum() > 10 and (o_hit == 0).sum() > 10
+    r = cb.collide(A, B, Pd)
+    assert (r.hit.cpu().numpy() == o_hit).all()
+    assert (r.offsets.cpu().numpy() == o_off).all()
+    assert (r.pairs.cpu().numpy() == o_ij).all()
+    o_d, _ = oracle.distance(field["Ao"], field["Bo"], P)
+    d = cb.distance(A, B, Pd).cpu().numpy()
+    assert np.abs(d - o_d).max() <= TOL_PQ * field["D"]
+    assert ((d == 0) == (o_d == 0)).all()

@@ -1,7 +1,8 @@
 """The request loop (continuous batching): every request's result is the same whether it is
 served alone or batched with others (CD bit-exact, PQ within 1e-5 D), under concurrent
 submission from several planner threads and under a memory budget that forces admission
-to wait."""
+to wait; chain robots (one pose per link) resolve to any-link collision and the smallest
+distance over their links."""
 import threading
 
 import numpy as np
@@ -33,13 +34,20 @@ def models(cb):
         terrain=cb.BVH(va, ta, 18, 4, 16, 4096), link=cb.BVH(*link, 18, 4, 16, 4096))
 
 
+ROBOTS = {"chain": ["link", "sphereB"]}
+
+
 def _requests(seed, count):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
-        env, robot = [("sphereA", "sphereB"), ("terrain", "sphereB"), ("terrain", "link"), ("sphereA", "link")][i % 4]
+        env, robot = [("sphereA", "sphereB"), ("terrain", "sphereB"), ("terrain", "link"), ("sphereA", "link"),
+                      ("terrain", "chain")][i % 5]
         n = int(np.exp(rng.uniform(0, np.log(300))))
-        P = synth.poses_box(n, seed=int(rng.integers(1 << 30)), lo=-1.5, hi=1.5)
+        if robot == "chain":
+            P = np.stack([synth.poses_box(n, seed=int(rng.integers(1 << 30)), lo=-1.5, hi=1.5) for _ in range(2)], 1)
+        else:
+            P = synth.poses_box(n, seed=int(rng.integers(1 << 30)), lo=-1.5, hi=1.5)
         kind = "collide" if rng.uniform() < 0.5 else "distance"
         out.append((env, robot, kind, P, bool(kind == "collide" and rng.uniform() < 0.5)))
     return out
@@ -47,17 +55,22 @@ def _requests(seed, count):
 
 def _alone(cb, models, env, robot, kind, P, early):
     import torch
-    Pd = torch.as_tensor(P, device="cuda")
-    if kind == "collide":
-        return cb.collide(models[env], models[robot], Pd, pairs=False, early_exit=early).hit.cpu().numpy()
-    return cb.distance(models[env], models[robot], Pd).cpu().numpy()
+    names = ROBOTS.get(robot, [robot])
+    res = []
+    for i, name in enumerate(names):
+        Pd = torch.as_tensor(np.ascontiguousarray(P[:, i] if len(names) > 1 else P), device="cuda")
+        if kind == "collide":
+            res.append(cb.collide(models[env], models[name], Pd, pairs=False, early_exit=early).hit.cpu().numpy())
+        else:
+            res.append(cb.distance(models[env], models[name], Pd).cpu().numpy())
+    return np.maximum.reduce(res) if kind == "collide" else np.minimum.reduce(res)
 
 
 @pytest.mark.parametrize("budget", [1 << 31, 600 << 20])
 def test_served_results_equal_alone(cb, models, budget):
     from paper_2012_05348_gb300.serve import Server
     reqs = _requests(11, 48)
-    srv = Server(models, mem_budget=budget)
+    srv = Server(models, mem_budget=budget, robots=ROBOTS)
     futures = [None] * len(reqs)
 
     def planner(k):
