@@ -216,9 +216,9 @@ def arm_sweep(cb, torch, dev, n_configs):
     def plain():
         for L, P in zip(links, LP):
             cb.collide(A, L, P, pairs=False, early_exit=True, check=False)
-    cb.set_option(cb.OPT_SPLIT, 0)
+    cb.set_option(cb.OPT_SPLIT, cb.SPLIT_POSE)
     ms_plain = _events_ms(plain, torch, reps=2)
-    cb.set_option(cb.OPT_SPLIT, 1)
+    cb.set_option(cb.OPT_SPLIT, cb.SPLIT_DEFAULT)
     q = 6 * n_configs
     return {"workload": f"6-link DH arm (5,120..40k tris per link) vs 1,026,400-tri clutter, {n_configs} configurations, "
                         "early-exit CD, 24-DOP m=8 8-bit 16 KB treelets",

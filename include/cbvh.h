@@ -188,9 +188,16 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
  *   off: on the terrain workload the top treelets are L1-resident anyway and staging costs
  *   occupancy).  Takes effect for queries issued afterwards. */
 #define CBVH_OPT_STAGE_BYTES 1
-/*   CBVH_OPT_SPLIT: work mapping.  1 (default): a pose's node-pair tree is split into tasks
- *   that later rounds spread over all warps (warp per node pair); 0: one round in which
- *   each warp traverses whole poses (warp per pose). */
+/*   CBVH_OPT_SPLIT: work mapping (scheduling only; results do not change).
+ *     0: one persistent launch in which each warp traverses whole poses (warp per pose).
+ *     1: rounds of persistent launches: a task that exceeds its expansion budget hands its
+ *        node-pair stack on as tasks for the next round (warp per node pair); the last
+ *        round runs every task to the end.
+ *     2: one launch over a work queue: warps take poses, then the tasks that busy warps
+ *        donate from the bottom of their stacks while other warps wait (work donation).
+ *     3: the rounds of 1, with the last round run as the work queue of 2.
+ *     4 (default): 2 for collision detection with pair lists, 3 for early-exit collision
+ *        detection (including every query without pair outputs) and proximity queries. */
 #define CBVH_OPT_SPLIT 2
 /*   CBVH_OPT_BUDGET0: node-pair expansions a task may run in round 0 before it hands the rest
  *   of its work on (default 256; later rounds allow 2, 4, 8 and 32 times as many, the last

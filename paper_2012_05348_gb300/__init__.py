@@ -20,7 +20,8 @@ from . import _build
 
 __all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
            "set_option", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
-           "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
+           "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "SPLIT_POSE", "SPLIT_ROUNDS", "SPLIT_QUEUE", "SPLIT_ROUNDS_QUEUE", "SPLIT_AUTO",
+           "SPLIT_DEFAULT", "BUDGET0_DEFAULT", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
 LIB_PATH = _build.LIB
 EARLY_EXIT = 1
@@ -172,6 +173,11 @@ OPT_SPLIT = 2
 OPT_BUDGET0 = 3
 OPT_TREELET_PACKING = 4
 PACK_TOP_DOWN, PACK_BOTTOM_UP = 0, 1
+# CBVH_OPT_SPLIT values: warp per pose, rounds, work queue, rounds then work queue, and the
+# default (work queue for collision with pair lists, rounds then work queue otherwise)
+SPLIT_POSE, SPLIT_ROUNDS, SPLIT_QUEUE, SPLIT_ROUNDS_QUEUE, SPLIT_AUTO = 0, 1, 2, 3, 4
+SPLIT_DEFAULT = SPLIT_AUTO
+BUDGET0_DEFAULT = 256
 
 
 def set_option(option: int, value: int) -> None:

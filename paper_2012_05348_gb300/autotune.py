@@ -16,11 +16,11 @@ import os
 
 import numpy as np
 
-from . import (BVH, OPT_BUDGET0, OPT_SPLIT, OPT_STAGE_BYTES, collide, distance, profile_collect, profile_enable,
-               set_option)
+from . import (BUDGET0_DEFAULT, BVH, OPT_BUDGET0, OPT_SPLIT, OPT_STAGE_BYTES, OPT_TREELET_PACKING, PACK_TOP_DOWN,
+               SPLIT_DEFAULT, collide, distance, profile_collect, profile_enable, set_option)
 
 DEFAULT_SPACE = dict(branching=(4, 8, 16), treelet_bytes=(4096, 16384, 65536), quant_bits=(8, 16),
-                     stage_bytes=(0, 16384), split=(1, 0), budget0=(64, 256, 1024))
+                     stage_bytes=(0, 16384), split=(4, 1, 2, 3, 0), budget0=(64, 256, 1024))
 
 
 def mesh_key(verts_a, tris_a, verts_b, tris_b, k: int, kind: str) -> str:
@@ -93,5 +93,5 @@ def apply(config: dict) -> None:
     """Set the launch options of a tuned configuration (the hierarchy parameters are used when
     building the BVHs); an empty dict restores the defaults."""
     set_option(OPT_STAGE_BYTES, int(config.get("stage_bytes", 0)))
-    set_option(OPT_SPLIT, int(config.get("split", 1)))
-    set_option(OPT_BUDGET0, int(config.get("budget0", 256)))
+    set_option(OPT_SPLIT, int(config.get("split", SPLIT_DEFAULT)))
+    set_option(OPT_BUDGET0, int(config.get("budget0", BUDGET0_DEFAULT)))

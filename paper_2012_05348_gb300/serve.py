@@ -102,8 +102,9 @@ class Server:
     # ---------------------------------------------------------------- serving thread
     @staticmethod
     def _bytes(n_poses: int) -> int:
-        # poses + outputs + the batch workspace's per-pose share (task buffers) + a fixed part
-        return n_poses * (48 + 4 + 1 + 2 * 16 * 256) + (96 << 20)
+        # poses + outputs + the batch workspace: two task buffers of 16-byte entries and their
+        # ready flags (at least 2^22 entries, else 512 per pose) + stacks and counters
+        return n_poses * (48 + 4 + 1) + max(1 << 22, 512 * n_poses) * (2 * 16 + 4) + (96 << 20)
 
     @staticmethod
     def _link_poses(r) -> int:

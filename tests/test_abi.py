@@ -126,3 +126,4 @@ def test_batch_rejects_unattached_handles(cb):
     assert cb.lib.cbvh_set_option(99, 0) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_STAGE_BYTES, 1 << 20) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_TREELET_PACKING, 2) == -1
+    assert cb.lib.cbvh_set_option(cb.OPT_SPLIT, 5) == -1

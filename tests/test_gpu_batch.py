@@ -2,7 +2,9 @@
 
 - Every item of a mixed batch (different pairs of hierarchies, collision with and without
   early exit, distances) returns exactly what the same query returns on its own.
-- The batch launch can be captured in a CUDA graph; replays reproduce the direct results.
+- The batch launch can be captured in a CUDA graph; replays reproduce the direct results,
+  with every scheduler (rounds of handed-on tasks, one launch over a work queue, or
+  rounds ending in a work-queue round).
 - A reduced arm-against-clutter sweep agrees with the FP64 oracle on poses away from contact.
 """
 import numpy as np
@@ -75,7 +77,16 @@ def test_batch_items_equal_single_queries(cb, scene):
     assert 0 < hits.any(0).sum() < hits.shape[1]  # some configurations collide, some do not
 
 
-def test_batch_graph_capture_and_replay(cb, scene):
+@pytest.mark.parametrize("split", [1, 2, 3, 4])
+def test_batch_graph_capture_and_replay(cb, scene, split):
+    cb.set_option(cb.OPT_SPLIT, split)
+    try:
+        _graph_replay(cb, scene)
+    finally:
+        cb.set_option(cb.OPT_SPLIT, cb.SPLIT_DEFAULT)
+
+
+def _graph_replay(cb, scene):
     import torch
     items = _items(scene)
     batch = cb.Batch(items)

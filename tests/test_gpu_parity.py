@@ -309,10 +309,12 @@ def test_c2_full_size_sampled_against_oracle(cb, c2):
             assert (np.diff(key) > 0).all()
 
 
-@pytest.mark.parametrize("stage,split,budget0", [(16384, 1, 16), (32768, 1, 256), (0, 0, 256)])
+@pytest.mark.parametrize("stage,split,budget0", [(16384, 1, 16), (32768, 3, 256), (0, 0, 256), (0, 1, 256),
+                                                (0, 2, 256), (16384, 2, 64), (0, 3, 16), (0, 4, 1024)])
 def test_launch_options_keep_results(cb, c1, c2, stage, split, budget0):
-    """Treelet staging in shared memory (TMA bulk copies), the warp-per-pose mapping and the
-    task budget change how the work is scheduled, never the result."""
+    """Treelet staging in shared memory (TMA bulk copies), the work mapping (warp per pose,
+    rounds of handed-on tasks, or one launch over a work queue with donation) and the task
+    budget change how the work is scheduled, never the result."""
     import torch
     P1 = _gpu(c1["P"])
     P2 = _gpu(c2["c"]["poses"][:1500])
@@ -326,8 +328,8 @@ def test_launch_options_keep_results(cb, c1, c2, stage, split, budget0):
                cb.collide(c2["A"], c2["B"], P2), cb.distance(c2["A"], c2["B"], P2).cpu().numpy())
     finally:
         cb.set_option(cb.OPT_STAGE_BYTES, 0)
-        cb.set_option(cb.OPT_SPLIT, 1)
-        cb.set_option(cb.OPT_BUDGET0, 256)
+        cb.set_option(cb.OPT_SPLIT, cb.SPLIT_DEFAULT)
+        cb.set_option(cb.OPT_BUDGET0, cb.BUDGET0_DEFAULT)
     for r, g in ((ref[0], got[0]), (ref[2], got[2])):
         assert torch.equal(r.hit, g.hit) and torch.equal(r.offsets, g.offsets) and torch.equal(r.pairs, g.pairs)
     assert np.allclose(ref[1], got[1], rtol=0, atol=1e-5 * c1["D"])
