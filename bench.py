@@ -8,8 +8,12 @@ triangles) and B = displaced level-5 icosphere (20,480 triangles); 24-DOP, branc
 triangle pair (sorted CSR lists) for all poses, then PQ (minimum distance) for all poses.
 Metric: pose queries/s, a CD query and a PQ query of one pose counting as two.
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
-bounded sample of the same poses.
+Prints one JSON line (rank 0).  After the timed headline step the same line carries the
+comparisons of `--sections`: the batched arm sweep against one query per link and launch,
+the served request loop against one call per request, and the scale-and-compression
+workload (a 10M-triangle field that does not fit in L2) at every compression setting.
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the same
+poses; `--scale-only` runs just the scale comparison (an entry point for profiling).
 """
 from __future__ import annotations
 
@@ -51,6 +55,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
     ap.add_argument("--arm-configs", type=int, default=200000)
+    ap.add_argument("--sections", default="batched,served,scale",
+                    help="comparisons run after the headline step: batched, served, scale (comma list)")
+    ap.add_argument("--scale-poses", type=int, default=1_000_000)
+    ap.add_argument("--scale-pq-poses", type=int, default=20_000)
+    ap.add_argument("--scale-pair-poses", type=int, default=100_000)
+    ap.add_argument("--scale-only", action="store_true",
+                    help="run only the scale-and-compression comparison (a profiling entry point)")
     return ap.parse_args()
 
 
@@ -289,6 +300,106 @@ def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 100
     return out
 
 
+def _bv_bytes(k: int, bits: int) -> int:
+    """Algorithmic bytes of one BV-pair test: A's k/2 slabs (2 values each) + 4 B topology,
+    and B's axis box (3 slabs); FP32 values when bits = 0."""
+    w = 4 if bits == 0 else bits // 8
+    return (k // 2) * 2 * w + 4 + 3 * 2 * w
+
+
+def scale(cb, torch, dev, n_poses, pq_poses, pair_poses):
+    """Scale and compression: 32 fractal-displaced level-7 spheres (10,485,760 triangles) in a
+    20 m cube, probed by a displaced level-6 sphere (81,920 triangles); 18-DOP, branching 4,
+    bottom-up treelets.  For 8- and 16-bit deltas at 16 and 128 KB treelets and for FP32
+    bounds: footprint, collision flags for every pose (each pose stops at its first pair),
+    collision with sorted pair lists on the first poses, distances on the first poses, and
+    the algorithmic bytes each query moves per second.  The hierarchy (about 1-1.8 GB) does
+    not fit in L2, so HBM is the roofline here."""
+    import ctypes as C
+    L = cb.lib
+    sp = cb._stream_ptr(None)
+    c = synth.C5(n_poses)
+    P = torch.as_tensor(c["poses"], device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_BOTTOM_UP)
+    out = []
+    try:
+        B = cb.BVH(*c["B"], 18, 4, 8, 16384, device=dev)
+
+        def run(A, n, kind, cap=0):
+            Pq = P[:n]
+            status = torch.zeros(1, dtype=torch.int32, device=dev)
+            if kind == "dist":
+                wsb = cb.workspace_bytes(A, B, n, 1)
+                ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+                dist = torch.empty(n, dtype=torch.float32, device=dev)
+                args = (A.handle, B.handle, C.c_void_p(Pq.data_ptr()), n, C.c_void_p(dist.data_ptr()),
+                        C.c_void_p(ws.data_ptr()), wsb, C.c_void_p(status.data_ptr()), sp)
+                fn = lambda: L.cbvh_distance(*args)  # noqa: E731
+            else:
+                wsb = cb.workspace_bytes(A, B, n, 0, cap)
+                ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+                hit = torch.empty(n, dtype=torch.uint8, device=dev)
+                off = torch.empty(n + 1, dtype=torch.int64, device=dev) if cap else None
+                prs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev) if cap else None
+                need = torch.zeros(1, dtype=torch.int64, device=dev)
+                ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
+                args = (A.handle, B.handle, C.c_void_p(Pq.data_ptr()), n, C.c_void_p(hit.data_ptr()), ptr(off),
+                        ptr(prs), cap, C.c_void_p(need.data_ptr()), cb.SORT_PAIRS if cap else 0,
+                        C.c_void_p(ws.data_ptr()), wsb, C.c_void_p(status.data_ptr()), sp)
+                fn = lambda: L.cbvh_collide(*args)  # noqa: E731
+            flush.zero_()
+            torch.cuda.synchronize()
+            cb.profile_collect()
+            cb.profile_enable(True)
+            rc = fn()
+            torch.cuda.synchronize()
+            cb.profile_enable(False)
+            pr = cb.profile_collect()
+            code = rc or int(status.item())
+            if kind == "pairs" and code == -4:  # pair capacity: the device reported the size needed
+                return run(A, n, kind, cap=int(need.item()) + 1024)
+            if code:
+                raise cb.CbvhError(code, L.cbvh_last_error().decode())
+            ms = pr["distance"][0] if kind == "dist" else pr["collide"][0]
+            extra = {}
+            if kind == "pairs":
+                extra["pairs"] = int(need.item())
+                extra["compaction_ms"] = pr["compaction"][0]
+            if kind != "dist":
+                extra["hits"] = int(hit.sum().item())
+            return ms, cb.query_stats(ws), extra
+
+        for bits, tb in [(8, 16384), (16, 16384), (0, 16384), (8, 131072)]:
+            t0 = time.perf_counter()
+            A = cb.BVH(*c["A"], 18, 4, bits, tb, device=dev)
+            build_s = time.perf_counter() - t0
+            bvb = _bv_bytes(18, bits)
+            r = {"quant_bits": bits, "treelet_bytes": tb, "node_bytes": A.info["node_bytes"],
+                 "blob_bytes": A.info["blob_bytes"], "treelets": A.info["n_treelets"], "host_build_s": build_s}
+            ms, (bv, leaf, _), ex = run(A, n_poses, "hits")
+            r["cd_flags"] = {"poses": n_poses, "ms": ms, "pose_queries_per_s": n_poses / (ms / 1e3),
+                             "hits": ex["hits"], "bv_tests": bv, "leaf_tests": leaf,
+                             "algorithmic_gbs": (bv * bvb + leaf * BYTES_LEAF + n_poses * 49) / (ms * 1e6)}
+            if bits == 8 and tb == 16384 and pair_poses:
+                ms, (bv, leaf, _), ex = run(A, pair_poses, "pairs", cap=2000 * pair_poses)
+                r["cd_pairs"] = {"poses": pair_poses, "ms": ms, "compaction_ms": ex["compaction_ms"],
+                                 "pose_queries_per_s": pair_poses / (ms / 1e3), "pairs": ex["pairs"],
+                                 "algorithmic_gbs": (bv * bvb + leaf * BYTES_LEAF + pair_poses * 57
+                                                     + ex["pairs"] * 12) / (ms * 1e6)}
+            ms, (bv, leaf, _), _ = run(A, pq_poses, "dist")
+            r["pq"] = {"poses": pq_poses, "ms": ms, "pose_queries_per_s": pq_poses / (ms / 1e3), "bv_tests": bv,
+                       "leaf_tests": leaf, "algorithmic_gbs": (bv * bvb + leaf * BYTES_LEAF + pq_poses * 52) / (ms * 1e6)}
+            out.append(r)
+            del A
+            torch.cuda.empty_cache()
+    finally:
+        cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
+    return {"workload": "32 fractal level-7 spheres (10,485,760 tris) in a 20 m cube vs displaced level-6 sphere "
+                        "(81,920 tris), 18-DOP, branching 4, bottom-up treelets; L2 flushed before each query",
+            "variants": out}
+
+
 # ------------------------------------------------------------------ engine
 def main():
     args = parse()
@@ -300,6 +411,11 @@ def main():
     import paper_2012_05348_gb300 as cb
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.scale_only:
+        if rank == 0:
+            print(json.dumps({"scale": scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses,
+                                             args.scale_pair_poses)}), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -437,8 +553,10 @@ def main():
         except (OSError, ValueError):
             traffic = None
     extra = {}
-    if not args.no_extra:
+    sections = set() if args.no_extra else {x.strip() for x in args.sections.split(",") if x.strip()}
+    if "batched" in sections:
         extra["batched"] = arm_sweep(cb, torch, dev, args.arm_configs)
+    if "served" in sections:
         c3 = synth.C3(8)
         models = {"terrain": A, "clutter": cb.BVH(*c3["A"], 24, 8, 8, 16384, device=dev), "sphere5": B,
                   "sphere3": cb.BVH(*synth.C1(1)["B"], 24, 8, 8, 16384, device=dev)}
@@ -446,6 +564,10 @@ def main():
             models[f"link{i}"] = cb.BVH(*link, 24, 8, 8, 16384, device=dev)
         robots = {"arm": [f"link{i}" for i in range(6)]}
         extra["served"] = serving(cb, torch, dev, models, robots, c["height"])
+        del models
+    if "scale" in sections:
+        torch.cuda.empty_cache()
+        extra["scale"] = scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses, args.scale_pair_poses)
     cpu = None
     if not args.no_cpu_baseline:
         rate, done, secs, cores = oracle_rate(c, args.cpu_sample)

@@ -4,6 +4,8 @@ displaced sphere, with bottom-up packed treelets at 8 and 16 bits and with FP32 
 - A reduced field (6 level-4 spheres in a 6 m cube, level-3 probe) against the FP64 oracle
   in full: collision bit-exact on poses away from contact, distances within 1e-5 of the
   scene diameter, for every compression setting.
+- The full field (32 level-7 spheres, 1,000,000 poses) at the benchmark's launch
+  configuration, checked by the oracle on a sample.
 """
 import numpy as np
 import pytest
@@ -60,3 +62,57 @@ def test_reduced_field_against_oracle(cb, field, bits, tb):
     d = cb.distance(A, B, Pd).cpu().numpy()
     assert np.abs(d - o_d).max() <= TOL_PQ * field["D"]
     assert ((d == 0) == (o_d == 0)).all()
+
+
+def _pairs_by_pose(off, ij):
+    return [ij[off[p]:off[p + 1]] for p in range(len(off) - 1)]
+
+
+def test_full_field_sampled_against_oracle(cb):
+    """The full 10,485,760-triangle field in the benchmark's launch configuration (8-bit,
+    16 KB bottom-up treelets): flags for all 1,000,000 poses, pair lists for the first
+    100,000, distances for the first 20,000.  The oracle checks a sample one by one;
+    near-contact pairs of the sample are compared as a set (certain <= GPU <= certain |
+    ambiguous)."""
+    import torch
+    c = synth.C5(1_000_000)
+    (va, ta), (vb, tb) = c["A"], c["B"]
+    A = cb.BVH(va, ta, 18, 4, 8, 16384)
+    B = cb.BVH(vb, tb, 18, 4, 8, 16384)
+    P = c["poses"]
+    Pd = torch.as_tensor(P, device="cuda")
+    flags = cb.collide(A, B, Pd, pairs=False).hit.cpu().numpy()
+    res = cb.collide(A, B, Pd[:100_000], capacity=250_000_000)
+    hit = res.hit.cpu().numpy()
+    pairs = _pairs_by_pose(res.offsets.cpu().numpy(), res.pairs.cpu().numpy())
+    dist = cb.distance(A, B, Pd[:20_000]).cpu().numpy()
+    assert (flags[:100_000] == hit).all()
+    del res
+    Ao = oracle.BVH(va, ta, 18, 4, 8, 16384, packing=oracle.PACKING_BOTTOM_UP)
+    Bo = oracle.BVH(vb, tb, 18, 4, 8, 16384, packing=oracle.PACKING_BOTTOM_UP)
+    D = synth.scene_diameter(va, vb)
+    eps = EPS_NEAR * D
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(20_000, 24, replace=False))
+    far = np.sort(rng.choice(np.arange(100_000, 1_000_000), 24, replace=False))
+    o_hit, o_off, o_ij, _ = oracle.collide(Ao, Bo, P[idx])
+    o_pairs = _pairs_by_pose(o_off, o_ij)
+    n_off, n_ij = oracle.near_pairs(Ao, Bo, P[idx], eps)
+    amb = _pairs_by_pose(n_off, n_ij)
+    key = lambda a: set(map(tuple, np.asarray(a).tolist()))  # noqa: E731
+    exact = 0
+    for q, p in enumerate(idx):
+        gpu, ora, am = key(pairs[p]), key(o_pairs[q]), key(amb[q])
+        certain = ora - am
+        assert certain <= gpu <= (ora | am), (p, len(certain - gpu), len(gpu - (ora | am)))
+        if not am:
+            exact += 1
+            assert gpu == ora and hit[p] == o_hit[q]
+    assert exact >= 12
+    o_d, _ = oracle.distance(Ao, Bo, P[idx])
+    assert np.abs(dist[idx] - o_d).max() <= TOL_PQ * D
+    # flags of poses beyond the pair-list prefix
+    f_hit, *_ = oracle.collide(Ao, Bo, P[far])
+    near, _ = oracle.near_contact(Ao, Bo, P[far], eps)
+    assert (flags[far][~near] == f_hit[~near]).all()
+    assert o_hit.sum() + f_hit.sum() >= 4 and (o_hit == 0).sum() >= 4
