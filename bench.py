@@ -200,44 +200,61 @@ def _events_ms(fn, torch, reps=3):
     return e0.elapsed_time(e1) / reps
 
 
-def arm_sweep(cb, torch, dev, n_configs):
+def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
     """Motion-planning sweep: 6 arm links against a 1,026,400-triangle clutter scene, early-exit
-    CD for every configuration.  Batched (one set of persistent launches over all links,
-    replayed from a CUDA graph) against the plain traversal (one query per link and launch,
-    one warp per pose)."""
+    CD for every configuration.  The autotuner first picks branching, treelet size,
+    quantisation bits and launch options (work mapping, budget) on the first `tune_configs`
+    configurations.  Then the whole sweep runs batched (one set of persistent launches over
+    all links, replayed from a CUDA graph) against the plain traversal (one query per link
+    and launch, one warp per pose) on the same hierarchies."""
+    from paper_2012_05348_gb300.autotune import DEFAULT_LAUNCH, apply, autotune_batch
     c = synth.C3(n_configs)
-    A = cb.BVH(*c["A"], 24, 8, 8, 16384, device=dev)
-    links = [cb.BVH(*l, 24, 8, 8, 16384, device=dev) for l in c["links"]]
     LP = [torch.as_tensor(np.ascontiguousarray(c["link_poses"][:, i]), device=dev) for i in range(6)]
-    items = [dict(A=A, B=L, kind="collide", poses=P, early_exit=True) for L, P in zip(links, LP)]
-    batch = cb.Batch(items, device=dev)
-    outs = batch.run()
-    g = torch.cuda.CUDAGraph()
-    s = torch.cuda.Stream(device=dev)
-    s.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(s):
-        batch.launch(s)
-    torch.cuda.current_stream(dev).wait_stream(s)
-    torch.cuda.synchronize()
-    with torch.cuda.graph(g):
-        batch.launch()
-    ms_batched = _events_ms(g.replay, torch)
-    collide_cfg = np.stack([o.cpu().numpy() for o in outs]).any(0)
+    t0 = time.perf_counter()
+    best, trials = autotune_batch(c["A"], c["links"], [P[:tune_configs] for P in LP], k=24, kind="collide",
+                                  early_exit=True, space=dict(stage_bytes=(0,)), reps=1, device=dev)
+    tune_s = time.perf_counter() - t0
+    default = dict(branching=8, treelet_bytes=16384, quant_bits=8, packing=cb.PACK_TOP_DOWN, **DEFAULT_LAUNCH)
+    default_ms = next((ms for cfg, ms in trials if cfg == default), None)
+    best_ms = min(ms for _, ms in trials)
+    m, tb, bits = best["branching"], best["treelet_bytes"], best["quant_bits"]
+    apply(best)
+    try:
+        A = cb.BVH(*c["A"], 24, m, bits, tb, device=dev)
+        links = [cb.BVH(*l, 24, m, bits, tb, device=dev) for l in c["links"]]
+        items = [dict(A=A, B=L, kind="collide", poses=P, early_exit=True) for L, P in zip(links, LP)]
+        batch = cb.Batch(items, device=dev)
+        outs = batch.run()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            batch.launch(s)
+        torch.cuda.current_stream(dev).wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            batch.launch()
+        ms_batched = _events_ms(g.replay, torch)
+        collide_cfg = np.stack([o.cpu().numpy() for o in outs]).any(0)
 
-    def plain():
-        for L, P in zip(links, LP):
-            cb.collide(A, L, P, pairs=False, early_exit=True, check=False)
-    cb.set_option(cb.OPT_SPLIT, cb.SPLIT_POSE)
-    ms_plain = _events_ms(plain, torch, reps=2)
-    cb.set_option(cb.OPT_SPLIT, cb.SPLIT_DEFAULT)
+        def plain():
+            for L, P in zip(links, LP):
+                cb.collide(A, L, P, pairs=False, early_exit=True, check=False)
+        cb.set_option(cb.OPT_SPLIT, cb.SPLIT_POSE)
+        ms_plain = _events_ms(plain, torch, reps=2)
+    finally:
+        apply({})
     q = 6 * n_configs
     return {"workload": f"6-link DH arm (5,120..40k tris per link) vs 1,026,400-tri clutter, {n_configs} configurations, "
-                        "early-exit CD, 24-DOP m=8 8-bit 16 KB treelets",
+                        "early-exit CD, 24-DOP",
+            "autotuned": {"best": best, "sample_configurations": tune_configs, "candidates": len(trials),
+                          "tuning_s": tune_s, "sample_ms_best": best_ms, "sample_ms_default": default_ms},
             "link_queries": q, "configs_in_collision": int(collide_cfg.sum()),
             "batched_link_queries_per_s": q / (ms_batched / 1e3), "batched_ms": ms_batched,
             "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,
-            "speedup_vs_plain": ms_plain / ms_batched, "batched": "one graph-captured persistent launch set",
-            "plain": "one cbvh_collide per link, one warp per pose"}
+            "speedup_vs_plain": ms_plain / ms_batched,
+            "batched": "one graph-captured persistent launch set, autotuned hierarchy and launch options",
+            "plain": "one cbvh_collide per link, one warp per pose, same hierarchies"}
 
 
 def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 10000, 50000), max_requests=400,
