@@ -41,8 +41,11 @@ constexpr int kMaxM = 16;   // branching factor
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = 32 * kWarpsPerBlock;
+// Resident blocks per SM the register allocation must allow: 5 for the single-query
+// collision kernel (93 registers, no spills; 20 warps per SM instead of 16), 4 otherwise
+// (fewer registers would spill in the distance and batch kernels).
 #ifndef CBVH_MIN_BLOCKS
-#define CBVH_MIN_BLOCKS 1
+#define CBVH_MIN_BLOCKS(MODE, BATCH) ((MODE) == 0 && !(BATCH) ? 5 : 4)
 #endif
 
 __constant__ int c_dir[kMaxK][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
@@ -642,7 +645,7 @@ __device__ __noinline__ int queue_take(const Params &p, unsigned int *qc, uint32
 }
 
 template <int MODE, int KA, bool BATCH>
-__global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS) traverse_kernel(const Params p) {
+__global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traverse_kernel(const Params p) {
   uint8_t *smem = g_dsmem;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
