@@ -48,6 +48,11 @@ constexpr int kThreads = 32 * kWarpsPerBlock;
 #define CBVH_MIN_BLOCKS(MODE, BATCH) ((MODE) == 0 && !(BATCH) ? 5 : 4)
 #endif
 
+// ceil(2^16 / n): (i * c_inv16[n]) >> 16 == i / n for 0 <= i < 256 and 1 <= n <= 16
+// (the rounding error i (c_inv16[n] - 2^16 / n) / 2^16 < 1 / 256 stays below 1 / n)
+__constant__ unsigned c_inv16[kMaxM + 1] = {0,    65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192,
+                                            7282, 6554,  5958,  5462,  5042,  4682,  4370,  4096};
+
 __constant__ int c_dir[kMaxK][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
                                     {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
                                     {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
@@ -236,10 +241,12 @@ __device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int la
 }
 
 // Decode the set that Algorithm 1 expands for node x -- its children, or x itself when x is
-// a leaf or `force_self` -- into per-member FP32 slab bounds (dirs < nd) written to lo/hi
-// (row stride KS), references to ref[], and leaf slots (or 0xffffffff) to leaf[].  Returns
+// a leaf or `force_self` -- into per-member FP32 slab bounds (lo, hi) of directions < ND,
+// written to iv (row stride KS), references to ref[], and leaf slots (or 0xffffffff) to
+// leaf[].  Returns
 // the number of members (warp-uniform).
-__device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float *lo, float *hi, int KS,
+template <int ND>
+__device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float2 *iv, int KS,
                           uint32_t *ref, uint32_t *leaf, bool leaf_bounds = true) {
   const uint32_t t = x >> X.lbits;
   if (t != S.cur_t) {
@@ -251,7 +258,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
   const int nc = (int)((w0 >> 16) & 31u);
   const bool ext = (w0 >> 21) & 1u;
   const bool self = force_self || nc == 0;
-  const int nd = S.nd;
+  constexpr int nd = ND;
   if (self && nc == 0 && !leaf_bounds) {  // a leaf standing for itself, bounded by its triangle
     if (lane == 0) {
       ref[0] = x;
@@ -262,11 +269,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
   }
   if (X.bits == 0) {
     if (self) {
-      if (lane < nd) {
-        float2 f = abs_float(rx, lane);
-        lo[lane] = f.x;
-        hi[lane] = f.y;
-      }
+      if (lane < nd) iv[lane] = abs_float(rx, lane);
       if (lane == 0) {
         ref[0] = x;
         leaf[0] = nc == 0 ? w1 : 0xffffffffu;
@@ -283,9 +286,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
           cref = (t << X.lbits) | (w1 + i);
           rc = rec_at(X, S.cur_base, w1 + i);
         }
-        float2 f = abs_float(rc, j);
-        lo[i * KS + j] = f.x;
-        hi[i * KS + j] = f.y;
+        iv[i * KS + j] = abs_float(rc, j);
         if (j == 0) {
           const uint32_t cw0 = ld32(rc);
           ref[i] = cref;
@@ -300,11 +301,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     int2 P;
     chain_decode(X, S, x, lane, P);
     if (self) {
-      if (lane < nd) {
-        float2 f = lat_to_f(P, X.scale);
-        lo[lane] = f.x;
-        hi[lane] = f.y;
-      }
+      if (lane < nd) iv[lane] = lat_to_f(P, X.scale);
       if (lane == 0) {
         ref[0] = x;
         leaf[0] = nc == 0 ? w1 : 0xffffffffu;
@@ -328,9 +325,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
       rc = rec_at(X, S.cur_base, w1 + i);
       L = apply_delta(S.lat[d * nd + j], rc, X.bits, j);
     }
-    float2 f = lat_to_f(L, X.scale);
-    lo[i * KS + j] = f.x;
-    hi[i * KS + j] = f.y;
+    iv[i * KS + j] = lat_to_f(L, X.scale);
     if (j == 0) {
       const uint32_t cw0 = ld32(rc);
       ref[i] = cref;
@@ -503,42 +498,55 @@ __device__ __forceinline__ void load_pair(const float4 *atris, const float4 *btr
 
 enum { MODE_CD = 0, MODE_PQ = 1 };
 
-// Pose cache layout (floats): R[9], t[3], then per A-direction j: u[3], |u|[3], s_lo, s_hi, eta
-constexpr int kPoseJ = 9;
+// Pose cache layout (floats): R[9], t[3], then per A-direction j, 16-byte aligned: u[3],
+// |u|[3], s_lo, s_hi, eta and 3 unused
+constexpr int kPoseJ = 12;
 __device__ __forceinline__ float *pose_dir(float *pc, int j) { return pc + 12 + kPoseJ * j; }
 constexpr int kStageBytesDefault = 0;  // per hierarchy and block: leading treelets staged in shared memory
 
 // Conservative interval of d_j . (R x + t) over B-member i: the exact posed triangle when the
-// member is a leaf, otherwise its decoded axis box.  q = pose_dir(pc, j).
-__device__ __forceinline__ float2 project_member(const float4 *btris, const float *q, const float *blo,
-                                                 const float *bhi, uint32_t leaf, int i) {
+// member is a leaf, otherwise its decoded axis box, given as centre and radius bound
+// bc[i] = (c, M = sum |c| + h) and half-size bh[i] = (h, 0).  q = pose_dir(pc, j).
+__device__ __forceinline__ float2 project_member(const float4 *btris, const float *q, const float4 *bc,
+                                                 const float4 *bh, uint32_t leaf, int i) {
+  const float4 q0 = reinterpret_cast<const float4 *>(q)[0];  // u[0..2], |u|[0]
+  const float4 q1 = reinterpret_cast<const float4 *>(q)[1];  // |u|[1..2], s_lo, s_hi
+  const float eta = q[8];
   if (leaf != 0xffffffffu) {
     const float4 *T = btris + 3 * (size_t)leaf;
     float lo = INFINITY, hi = -INFINITY;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
       const float4 x = T[v];
-      const float l = __fmaf_rd(q[0], x.x, __fmaf_rd(q[1], x.y, __fmaf_rd(q[2], x.z, q[6])));
-      const float h = __fmaf_ru(q[0], x.x, __fmaf_ru(q[1], x.y, __fmaf_ru(q[2], x.z, q[7])));
-      const float sl = __fmul_ru(q[8], __fadd_ru(__fadd_ru(fabsf(x.x), fabsf(x.y)), fabsf(x.z)));
+      const float l = __fmaf_rd(q0.x, x.x, __fmaf_rd(q0.y, x.y, __fmaf_rd(q0.z, x.z, q1.z)));
+      const float h = __fmaf_ru(q0.x, x.x, __fmaf_ru(q0.y, x.y, __fmaf_ru(q0.z, x.z, q1.w)));
+      const float sl = __fmul_ru(eta, __fadd_ru(__fadd_ru(fabsf(x.x), fabsf(x.y)), fabsf(x.z)));
       lo = fminf(lo, __fsub_rd(l, sl));
       hi = fmaxf(hi, __fadd_ru(h, sl));
     }
     return make_float2(lo, hi);
   }
+  const float4 c = bc[i], h = bh[i];
+  const float mlo = __fmaf_rd(q0.x, c.x, __fmaf_rd(q0.y, c.y, __fmaf_rd(q0.z, c.z, q1.z)));
+  const float mhi = __fmaf_ru(q0.x, c.x, __fmaf_ru(q0.y, c.y, __fmaf_ru(q0.z, c.z, q1.w)));
+  const float rad = __fmaf_ru(q0.w, h.x, __fmaf_ru(q1.x, h.y, __fmul_ru(q1.y, h.z)));
+  const float sl = __fmul_ru(eta, c.w);
+  return make_float2(__fsub_rd(__fsub_rd(mlo, rad), sl), __fadd_ru(__fadd_ru(mhi, rad), sl));
+}
+
+// Centre, half-size and sum |c| + h of B-member i's decoded axis box (conservative: the box
+// [c - h, c + h] contains [lo, hi] and M bounds sum |c| + h from above).
+__device__ __forceinline__ void member_box(const float2 *bvv, int i, float4 &bc, float4 &bh) {
   float c[3], h[3], M = 0.f;
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    const float lo = blo[i * 4 + x], hi = bhi[i * 4 + x];
-    c[x] = __fmul_rn(__fadd_rn(lo, hi), 0.5f);
-    h[x] = fmaxf(__fsub_ru(hi, c[x]), __fsub_ru(c[x], lo));
+    const float2 v = bvv[i * 4 + x];
+    c[x] = __fmul_rn(__fadd_rn(v.x, v.y), 0.5f);
+    h[x] = fmaxf(__fsub_ru(v.y, c[x]), __fsub_ru(c[x], v.x));
     M = __fadd_ru(M, __fadd_ru(fabsf(c[x]), h[x]));
   }
-  const float mlo = __fmaf_rd(q[0], c[0], __fmaf_rd(q[1], c[1], __fmaf_rd(q[2], c[2], q[6])));
-  const float mhi = __fmaf_ru(q[0], c[0], __fmaf_ru(q[1], c[1], __fmaf_ru(q[2], c[2], q[7])));
-  const float rad = __fmaf_ru(q[3], h[0], __fmaf_ru(q[4], h[1], __fmul_ru(q[5], h[2])));
-  const float sl = __fmul_ru(q[8], M);
-  return make_float2(__fsub_rd(__fsub_rd(mlo, rad), sl), __fadd_ru(__fadd_ru(mhi, rad), sl));
+  bc = make_float4(c[0], c[1], c[2], M);
+  bh = make_float4(h[0], h[1], h[2], 0.f);
 }
 
 // Treelet staging (Sec. III-B clusters the hierarchy into treelets sized to a cache; here the
@@ -677,15 +685,14 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
           staged ? (uint32_t)p.L.st_cnt[1] : 0u,
           p.L.st_off[1],
           p.L.st_toff[1]};
-  float *alo = reinterpret_cast<float *>(ws + p.L.o_aset);
-  float *ahi = alo + kMaxM * KS;
-  uint32_t *aref = reinterpret_cast<uint32_t *>(ahi + kMaxM * KS);
+  float2 *aiv = reinterpret_cast<float2 *>(ws + p.L.o_aset);  // A members' slabs (lo, hi) [i][KS]
+  uint32_t *aref = reinterpret_cast<uint32_t *>(aiv + kMaxM * KS);
   uint32_t *aleaf = aref + kMaxM;
-  float *blo = reinterpret_cast<float *>(ws + p.L.o_bset);  // B member axis boxes [i][0..2]
-  float *bhi = blo + kMaxM * 4;
-  float *plo = bhi + kMaxM * 4;  // B members projected on A's directions [i][KS]
-  float *phi = plo + kMaxM * KS;
-  uint32_t *bref = reinterpret_cast<uint32_t *>(phi + kMaxM * KS);
+  float2 *bvv = reinterpret_cast<float2 *>(ws + p.L.o_bset);  // B members' axis slabs [i][0..2]
+  float4 *bcm = reinterpret_cast<float4 *>(bvv + kMaxM * 4);  // B members' box centre and M [i]
+  float4 *bhm = bcm + kMaxM;                                   // ... and half-size [i]
+  float2 *piv = reinterpret_cast<float2 *>(bhm + kMaxM);      // B members projected on A's directions [i][KS]
+  uint32_t *bref = reinterpret_cast<uint32_t *>(piv + kMaxM * KS);
   uint32_t *bleaf = bref + kMaxM;
   for (int i = lane; i <= p.L.tdA; i += 32) SA.tag[i] = 0xffffffffu;
   for (int i = lane; i <= p.L.tdB; i += 32) SB.tag[i] = 0xffffffffu;
@@ -918,19 +925,19 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       // order one of them is often the same as in the previous expansion and is reused.
       int na, nb;
       if (a != keyA || root) {
-        na = decode_set(A, SA, a, root, lane, alo, ahi, KS, aref, aleaf);
+        na = decode_set<KA>(A, SA, a, root, lane, aiv, KS, aref, aleaf);
         keyA = root ? 0xffffffffu : a;
         na_c = na;
       } else {
         na = na_c;
       }
       if (b != keyB || root) {
-        nb = decode_set(B, SB, b, root, lane, blo, bhi, 4, bref, bleaf, false);
+        nb = decode_set<3>(B, SB, b, root, lane, bvv, 4, bref, bleaf, false);
+        if (lane < nb && bleaf[lane] == 0xffffffffu) member_box(bvv, lane, bcm[lane], bhm[lane]);
+        __syncwarp();
         for (int it = lane; it < nb * KA; it += 32) {
           const int i = it / KA, j = it - i * KA;
-          const float2 r = project_member(B.tris, pose_dir(pc, j), blo, bhi, bleaf[i], i);
-          plo[i * KS + j] = r.x;
-          phi[i * KS + j] = r.y;
+          piv[i * KS + j] = project_member(B.tris, pose_dir(pc, j), bcm, bhm, bleaf[i], i);
         }
         __syncwarp();
         keyB = root ? 0xffffffffu : b;
@@ -944,6 +951,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       // test every member pair; survivors are compacted by ballot onto the stack (inner
       // pairs) or the leaf queue (leaf pairs)
       const int np = na * nb;
+      const unsigned inv_nb = c_inv16[nb];  // it / nb == (it * inv_nb) >> 16 for it < 256
       n_bv += np;
       float run_lb = INFINITY;  // PQ: smallest lower bound pushed by this expansion ...
       int run_pos = -1;         // ... and its stack slot
@@ -953,13 +961,16 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         int i = 0, j = 0;
         float lb = INFINITY;
         if (it < np) {
-          i = it / nb;
+          i = (int)(((unsigned)it * inv_nb) >> 16);
           j = it - i * nb;
-          const float *al = alo + i * KS, *ah = ahi + i * KS, *pl = plo + j * KS, *ph = phi + j * KS;
+          const float2 *av = aiv + i * KS, *pv = piv + j * KS;
           if (MODE == MODE_CD) {
             keep = true;
 #pragma unroll
-            for (int d = 0; d < KA; ++d) keep &= (al[d] <= ph[d]) & (pl[d] <= ah[d]);
+            for (int d = 0; d < KA; ++d) {
+              const float2 x = av[d], y = pv[d];
+              keep &= (x.x <= y.y) & (y.x <= x.y);
+            }
           } else {
             // two lower bounds, all rounded down: the widest slab gap over |d|, and the
             // distance between the axis boxes, sqrt of the squared gaps along x, y and z
@@ -967,7 +978,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
             float box2 = 0.f;
 #pragma unroll
             for (int d = 0; d < KA; ++d) {
-              const float g = fmaxf(__fsub_rd(al[d], ph[d]), __fsub_rd(pl[d], ah[d]));
+              const float2 x = av[d], y = pv[d];
+              const float g = fmaxf(__fsub_rd(x.x, y.y), __fsub_rd(y.x, x.y));
               lb = fmaxf(lb, __fmul_rd(g, p.invn[d]));
               if (d < 3) {
                 const float gp = fmaxf(g, 0.f);
@@ -1375,8 +1387,8 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   o = align16(o + 4 * (tdB + 1));
   L.o_aset = o;
   o = align16(o + 4 * (2 * kMaxM * L.KS + 2 * kMaxM));
-  L.o_bset = o;
-  o = align16(o + 4 * (2 * kMaxM * 4 + 2 * kMaxM * L.KS + 2 * kMaxM));
+  L.o_bset = o;  // axis slabs (float2 x 4), box centre and half-size (float4 x 2), projections
+  o = align16(o + 4 * (2 * kMaxM * 4 + 8 * kMaxM + 2 * kMaxM * L.KS + 2 * kMaxM));
   L.o_bvd = o;
   o = align16(o + 2 * (int)sizeof(BVd));
   L.warp_bytes = o;
