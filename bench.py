@@ -10,7 +10,8 @@ Metric: pose queries/s, a CD query and a PQ query of one pose counting as two.
 
 Prints one JSON line (rank 0).  After the timed headline step the same line carries the
 comparisons of `--sections`: the batched arm sweep against one query per link and launch,
-the served request loop against one call per request, and the scale-and-compression
+the served request loop against one call per request, the terrain step under every way
+of storing the bounds (8/16-bit deltas, FP16, FP32), and the scale-and-compression
 workload (a 10M-triangle field that does not fit in L2) at every compression setting.
 `--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the same
 poses; `--scale-only` runs just the scale comparison (an entry point for profiling).
@@ -55,8 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
     ap.add_argument("--arm-configs", type=int, default=200000)
-    ap.add_argument("--sections", default="batched,served,scale",
-                    help="comparisons run after the headline step: batched, served, scale (comma list)")
+    ap.add_argument("--sections", default="batched,served,compression,scale",
+                    help="comparisons run after the headline step: batched, served, compression, scale "
+                         "(comma list)")
     ap.add_argument("--scale-poses", type=int, default=1_000_000)
     ap.add_argument("--scale-pq-poses", type=int, default=20_000)
     ap.add_argument("--scale-pair-poses", type=int, default=100_000)
@@ -317,10 +319,71 @@ def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 100
     return out
 
 
+def compression(cb, torch, dev, c, steps=3):
+    """The terrain step (CD with sorted pair lists + PQ, every pose) for each way of storing
+    the bounds: 8- and 16-bit predictor-corrector deltas, FP16 descriptors (the paper's
+    measured mode, Sec. III-A) and uncompressed FP32.  Same hierarchy shape (24-DOP,
+    branching 8, 16 KB treelets); L2 flushed before every step; kernel time from the
+    library's events."""
+    import ctypes as C
+    L = cb.lib
+    sp = cb._stream_ptr(None)
+    n = len(c["poses"])
+    P = torch.as_tensor(c["poses"], device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = []
+    for bits in (8, 16, 1, 0):
+        A = cb.BVH(*c["A"], K_DOP, BRANCH, bits, TREELET, device=dev)
+        B = cb.BVH(*c["B"], K_DOP, BRANCH, bits, TREELET, device=dev)
+        cap = 16_000_000
+        hit = torch.empty(n, dtype=torch.uint8, device=dev)
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        prs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+        need = torch.zeros(1, dtype=torch.int64, device=dev)
+        dist = torch.empty(n, dtype=torch.float32, device=dev)
+        st = torch.zeros(2, dtype=torch.int32, device=dev)
+        wc = cb.workspace_bytes(A, B, n, 0, cap)
+        wp = cb.workspace_bytes(A, B, n, 1)
+        ws_c = torch.empty(wc, dtype=torch.uint8, device=dev)
+        ws_p = torch.empty(wp, dtype=torch.uint8, device=dev)
+        ptr = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+        st1 = C.c_void_p(st.data_ptr() + 4)
+
+        def step():
+            rc = L.cbvh_collide(A.handle, B.handle, ptr(P), n, ptr(hit), ptr(off), ptr(prs), cap, ptr(need),
+                                cb.SORT_PAIRS, ptr(ws_c), wc, ptr(st), sp)
+            rc |= L.cbvh_distance(A.handle, B.handle, ptr(P), n, ptr(dist), ptr(ws_p), wp, st1, sp)
+            if rc:
+                raise cb.CbvhError(rc, L.cbvh_last_error().decode())
+        step()
+        torch.cuda.synchronize()
+        if int(st.abs().sum().item()):
+            raise RuntimeError("device status in the compression comparison")
+        ms = {"collide": 0.0, "distance": 0.0}
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            cb.profile_collect()
+            cb.profile_enable(True)
+            step()
+            torch.cuda.synchronize()
+            cb.profile_enable(False)
+            pr = cb.profile_collect()
+            ms["collide"] += pr["collide"][0] / steps
+            ms["distance"] += pr["distance"][0] / steps
+        out.append({"mode": {8: "8-bit deltas", 16: "16-bit deltas", 1: "FP16", 0: "FP32"}[bits],
+                    "quant_bits": bits, "node_bytes": A.info["node_bytes"], "cd_ms": ms["collide"],
+                    "pq_ms": ms["distance"], "pose_queries_per_s": 2 * n / ((ms["collide"] + ms["distance"]) / 1e3)})
+        del A, B
+        torch.cuda.empty_cache()
+    return {"workload": "terrain step (10,000 poses, CD with sorted pairs + PQ), 24-DOP, branching 8, 16 KB treelets",
+            "modes": out}
+
+
 def _bv_bytes(k: int, bits: int) -> int:
     """Algorithmic bytes of one BV-pair test: A's k/2 slabs (2 values each) + 4 B topology,
-    and B's axis box (3 slabs); FP32 values when bits = 0."""
-    w = 4 if bits == 0 else bits // 8
+    and B's axis box (3 slabs); FP32 values when bits = 0, FP16 values when bits = 1."""
+    w = 4 if bits == 0 else (2 if bits == 1 else bits // 8)
     return (k // 2) * 2 * w + 4 + 3 * 2 * w
 
 
@@ -387,7 +450,7 @@ def scale(cb, torch, dev, n_poses, pq_poses, pair_poses):
                 extra["hits"] = int(hit.sum().item())
             return ms, cb.query_stats(ws), extra
 
-        for bits, tb in [(8, 16384), (16, 16384), (0, 16384), (8, 131072)]:
+        for bits, tb in [(8, 16384), (16, 16384), (1, 16384), (0, 16384), (8, 131072)]:
             t0 = time.perf_counter()
             A = cb.BVH(*c["A"], 18, 4, bits, tb, device=dev)
             build_s = time.perf_counter() - t0
@@ -582,6 +645,8 @@ def main():
         robots = {"arm": [f"link{i}" for i in range(6)]}
         extra["served"] = serving(cb, torch, dev, models, robots, c["height"])
         del models
+    if "compression" in sections:
+        extra["compression"] = compression(cb, torch, dev, c)
     if "scale" in sections:
         torch.cuda.empty_cache()
         extra["scale"] = scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses, args.scale_pair_poses)

@@ -42,6 +42,7 @@ extern "C" {
 #define CBVH_ERR_STATE (-9)     /* handle has no device blob attached */
 
 /* collide flags */
+#define CBVH_QUANT_FP16 1 /* quant_bits value of the half-precision descriptor mode */
 #define CBVH_EARLY_EXIT 1u /* stop each pose at its first intersecting pair (pair outputs must be NULL);
                             * implied whenever no pair outputs are requested */
 #define CBVH_SORT_PAIRS 2u /* sort each pose's pair list by (i, j) */
@@ -73,8 +74,10 @@ const char *cbvh_last_error(void);
  *      split by log2(branching) rounds of median splits on the longest centroid axis.
  *   quant_bits: 8 or 16 -- slab bounds quantised on one lattice of step 2^e ("we quantify
  *      BV", abstract) and stored as predictor-corrector deltas (Sec. III-B): predictor =
- *      the parent's decoded interval, corrector = outward b-bit delta; 0 -- uncompressed
- *      FP32 bounds.
+ *      the parent's decoded interval, corrector = outward b-bit delta; CBVH_QUANT_FP16
+ *      (1) -- absolute half-precision bounds, lo rounded down and hi rounded up (the
+ *      half-float descriptors of Sec. III-A; bounds beyond +-65504 become infinite); 0 --
+ *      uncompressed FP32 bounds.
  *   treelet_bytes: power of two in [4096, 131072]; the hierarchy is clustered into treelets
  *      of at most this size (Sec. III-B), each with an absolute root for random access.
  * On success *out receives a handle owning host memory only; attach a device copy of its
@@ -97,7 +100,7 @@ int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *stream);
 
 /* Test hook: decode every node on the device, in blob order (treelet by treelet, local
  * index order).  lattice_out: n_nodes x (k/2) x 2 int32 decoded lattice bounds [lo, hi]
- * (not written when quant_bits = 0; may be NULL); bounds_out: n_nodes x (k/2) x 2 FP32
+ * (not written when quant_bits = 0 or 1; may be NULL); bounds_out: n_nodes x (k/2) x 2 FP32
  * bounds (lo rounded down, hi rounded up).  Asynchronous on `stream`. */
 int cbvh_decode_all(const cbvh_bvh *h, int32_t *lattice_out, float *bounds_out, void *stream);
 

@@ -57,6 +57,12 @@ def lib():
         L.or_floor_sum3.restype = I64
         L.or_ceil_sum3.argtypes = [D, D, D]
         L.or_ceil_sum3.restype = I64
+        L.or_half_rd.argtypes = [D]
+        L.or_half_rd.restype = C.c_uint32
+        L.or_half_ru.argtypes = [D]
+        L.or_half_ru.restype = C.c_uint32
+        L.or_half_value.argtypes = [C.c_uint32]
+        L.or_half_value.restype = D
         L.or_lattice_dv.argtypes = [P, I32, I32, P, P]
         L.or_tri_intersect.argtypes = [P, P, P]
         L.or_tri_intersect.restype = I32
@@ -260,6 +266,25 @@ def pt_tri(p, T) -> float:
 def seg_seg(a, b, c, d) -> float:
     f = lambda x: _p(np.ascontiguousarray(x, np.float64))  # noqa: E731
     return float(lib().or_seg_seg(f(a), f(b), f(c), f(d)))
+
+
+# quant_bits value of the half-precision descriptor mode
+QUANT_FP16 = 1
+
+
+def half_rd(v: float) -> int:
+    """Bits of the largest IEEE binary16 value <= v."""
+    return int(lib().or_half_rd(float(v)))
+
+
+def half_ru(v: float) -> int:
+    """Bits of the smallest IEEE binary16 value >= v."""
+    return int(lib().or_half_ru(float(v)))
+
+
+def half_value(bits: int) -> float:
+    """Value of an IEEE binary16 bit pattern."""
+    return float(lib().or_half_value(int(bits)))
 
 
 def floor_sum3(a: float, b: float, c: float) -> int:

@@ -112,6 +112,44 @@ static float f32_ru(int64_t L, int e) {
   return ldexpf(f, e);
 }
 
+/* IEEE 754 binary16 (the half floats of Sec. III-A): value of a bit pattern, by the format's
+ * definition -- sign, 5-bit exponent with bias 15, 10-bit fraction, subnormals at exponent 0,
+ * infinity at exponent 31 with zero fraction. */
+static double half_value(uint32_t h) {
+  int sign = (h >> 15) & 1, ex = (h >> 10) & 31, fr = h & 1023;
+  double v;
+  if (ex == 0)
+    v = ldexp((double)fr, -24);
+  else if (ex == 31)
+    v = INFINITY;
+  else
+    v = ldexp(1024.0 + fr, ex - 25);
+  return sign ? -v : v;
+}
+/* Outward rounding of v to half precision: the largest half <= v (down) or the smallest
+ * half >= v (up).  Non-negative patterns 0x0000..0x7c00 are ordered like their values, so
+ * a binary search over them finds the neighbours of |v|; negative v mirrors. */
+static uint32_t half_search(double a, int up) { /* a >= 0 */
+  uint32_t lo = 0, hi = 0x7c00u;
+  if (up) { /* smallest pattern with value >= a */
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) / 2;
+      if (half_value(mid) >= a) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+  }
+  while (lo < hi) { /* largest pattern with value <= a */
+    uint32_t mid = (lo + hi + 1) / 2;
+    if (half_value(mid) <= a) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+static uint32_t half_rd(double v) { return v >= 0 ? half_search(v, 0) : (0x8000u | half_search(-v, 1)); }
+static uint32_t half_ru(double v) { return v >= 0 ? half_search(v, 1) : (0x8000u | half_search(-v, 0)); }
+uint32_t or_half_rd(double v) { return half_rd(v); }
+uint32_t or_half_ru(double v) { return half_ru(v); }
+double or_half_value(uint32_t h) { return half_value(h); }
+
 /* ------------------------------------------------------------------ BVH */
 typedef struct {
   int k, K, m, bits, budget;
@@ -265,7 +303,8 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   if (packing != 0 && packing != 1) return fail(OR_ERR_ARG, "packing must be 0 or 1");
   if (k != 6 && k != 18 && k != 24 && k != 26) return fail(OR_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (m != 2 && m != 4 && m != 8 && m != 16) return fail(OR_ERR_ARG, "branching must be 2, 4, 8 or 16");
-  if (bits != 0 && bits != 8 && bits != 16) return fail(OR_ERR_ARG, "quant_bits must be 0, 8 or 16");
+  if (bits != 0 && bits != 1 && bits != 8 && bits != 16)
+    return fail(OR_ERR_ARG, "quant_bits must be 0 (FP32), 1 (FP16), 8 or 16");
   if (treelet_bytes < 4096 || treelet_bytes > 131072 || (treelet_bytes & (treelet_bytes - 1)))
     return fail(OR_ERR_ARG, "treelet_bytes must be a power of two in [4096, 131072]");
   if (nt < 1 || nt > 0x7fffffff || nv < 3 || nv > 0x7fffffff) return fail(OR_ERR_MESH, "bad mesh size");
@@ -280,6 +319,7 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   h->nt = nt;
   h->root_bytes = 8 + 8 * h->K;
   h->rec_bytes = bits == 0 ? h->root_bytes : ((8 + h->K * 2 * (bits / 8) + 3) / 4) * 4;
+  if (bits == 1) h->root_bytes = h->rec_bytes = 8 + 4 * h->K; /* absolute halves everywhere */
   if (16 + h->root_bytes + m * h->rec_bytes > treelet_bytes) {
     or_free(h);
     return fail(OR_ERR_ARG, "treelet_bytes too small for one sibling group");
@@ -432,6 +472,12 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
       }
     }
   }
+  if (h->bits == 1) /* half floats: every node's bounds, hence the root's, within +-65504 */
+    for (int j = 0; j < 2 * K; ++j)
+      if (fabs(ldexp((double)h->lat[j], h->e)) > 65504.0) {
+        or_free(h);
+        return fail(OR_ERR_MESH, "bounds beyond the half-precision range");
+      }
   int rc = encode(h);
   if (rc) {
     or_free(h);
@@ -619,7 +665,7 @@ static int encode(or_bvh *h) {
     const int64_t *C = h->lat + x * K * 2;
     int64_t *D = h->dec + x * K * 2;
     int is_root = h->local[x] == 0;
-    if (is_root || h->bits == 0) {
+    if (is_root || h->bits == 0 || h->bits == 1) {
       for (int j = 0; j < 2 * K; ++j) D[j] = C[j];
     } else {
       const int64_t *P = h->dec + (int64_t)h->parent[x] * K * 2;
@@ -636,8 +682,13 @@ static int encode(or_bvh *h) {
       }
     }
     for (int j = 0; j < K; ++j) {
-      h->decf[x * K * 2 + 2 * j] = f32_rd(D[2 * j], h->e);
-      h->decf[x * K * 2 + 2 * j + 1] = f32_ru(D[2 * j + 1], h->e);
+      if (h->bits == 1) { /* half precision, rounded outward from the exact lattice value */
+        h->decf[x * K * 2 + 2 * j] = (float)half_value(half_rd(ldexp((double)D[2 * j], h->e)));
+        h->decf[x * K * 2 + 2 * j + 1] = (float)half_value(half_ru(ldexp((double)D[2 * j + 1], h->e)));
+      } else {
+        h->decf[x * K * 2 + 2 * j] = f32_rd(D[2 * j], h->e);
+        h->decf[x * K * 2 + 2 * j + 1] = f32_ru(D[2 * j + 1], h->e);
+      }
     }
   }
 
@@ -704,7 +755,12 @@ static int encode(or_bvh *h) {
         w1 = (uint32_t)h->local[h->first[x]];
       put32(R, w0);
       put32(R + 4, w1);
-      if (l == 0 || h->bits == 0) {
+      if (h->bits == 1) {
+        for (int j = 0; j < K; ++j) {
+          put16(R + 8 + 4 * j, half_rd(ldexp((double)h->dec[x * K * 2 + 2 * j], h->e)));
+          put16(R + 10 + 4 * j, half_ru(ldexp((double)h->dec[x * K * 2 + 2 * j + 1], h->e)));
+        }
+      } else if (l == 0 || h->bits == 0) {
         for (int j = 0; j < K; ++j) {
           if (h->bits == 0) {
             put32(R + 8 + 8 * j, f2u(h->decf[x * K * 2 + 2 * j]));
@@ -817,7 +873,7 @@ static uint32_t get16(const uint8_t *p) { return (uint32_t)p[0] | ((uint32_t)p[1
 static uint64_t get64(const uint8_t *p) { return (uint64_t)get32(p) | ((uint64_t)get32(p + 4) << 32); }
 
 /* Decode every node of a blob, in blob order (treelet by treelet, local index order).
- * lat: n x K x 2 decoded lattice (not written for quant_bits = 0); f: n x K x 2 FP32
+ * lat: n x K x 2 decoded lattice (not written for quant_bits = 0 or 1); f: n x K x 2 FP32
  * bounds; meta: n x 4 (w0, w1, treelet, local).  Returns the node count, or < 0. */
 int64_t or_decode_blob(const uint8_t *blob, int64_t bytes, int32_t *lat, float *f, uint32_t *meta) {
   if (bytes < 64 || get32(blob) != 0x48564243u) return fail(OR_ERR_ARG, "not a blob");
@@ -840,6 +896,13 @@ int64_t or_decode_blob(const uint8_t *blob, int64_t bytes, int32_t *lat, float *
       uint32_t w0 = get32(R), w1 = get32(R + 4);
       int64_t *D = P + (int64_t)l * 2 * K;
       for (int j = 0; j < K; ++j) {
+        if (bits == 1) {
+          if (f) {
+            f[n * K * 2 + 2 * j] = (float)half_value(get16(R + 8 + 4 * j));
+            f[n * K * 2 + 2 * j + 1] = (float)half_value(get16(R + 10 + 4 * j));
+          }
+          continue;
+        }
         if (bits == 0) {
           float lo, hi;
           uint32_t a = get32(R + 8 + 8 * j), b = get32(R + 12 + 8 * j);

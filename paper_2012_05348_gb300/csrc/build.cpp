@@ -27,7 +27,9 @@
 //         u32 w1 = first child (local index, or treelet id when external) or, at a leaf,
 //         its leaf-order triangle slot; then per direction j the pair (lo, hi): absolute
 //         int32 lattice values at a treelet root, b-bit correctors elsewhere, or FP32
-//         values (lo rounded down, hi rounded up) everywhere when quant_bits = 0.
+//         values (lo rounded down, hi rounded up) everywhere when quant_bits = 0, or FP16
+//         values rounded the same way (Sec. III-A's half-float descriptors) everywhere when
+//         quant_bits = 1.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -196,6 +198,36 @@ void w32(std::vector<uint8_t> &b, int64_t o, uint32_t v) { std::memcpy(&b[o], &v
 void w64(std::vector<uint8_t> &b, int64_t o, uint64_t v) { std::memcpy(&b[o], &v, 8); }
 void w16(std::vector<uint8_t> &b, int64_t o, uint16_t v) { std::memcpy(&b[o], &v, 2); }
 
+// IEEE binary16 bits of the largest half-precision value <= v (down) or the smallest >= v
+// (up), for a finite double v.  Values beyond the largest finite half (65504) round to it
+// or to the infinity on their side, so the result always bounds v outward.  Positive v is
+// q * quantum with the quantum of v's binade (2^-24 below 2^-14), q taken by floor or ceil.
+uint16_t half_pos(double v, bool up) {  // v > 0
+  if (v > 65504.0) return up ? 0x7c00u : 0x7bffu;
+  int ex = 0;
+  std::frexp(v, &ex);  // v = f 2^ex, f in [0.5, 1): binade exponent E = ex - 1
+  const int E = std::max(ex - 1, -14);
+  const double quantum = std::ldexp(1.0, E - 10);
+  const double q = up ? std::ceil(v / quantum) : std::floor(v / quantum);  // exact: power-of-two scaling
+  int64_t qi = (int64_t)q;
+  if (E == -14 && qi < 1024) return (uint16_t)qi;  // subnormal (or the first normal when qi reaches 1024)
+  int exp_field = E + 15;
+  if (qi == 2048) {  // ceil reached the next binade
+    qi = 1024;
+    ++exp_field;
+  }
+  if (exp_field >= 31) return 0x7c00u;
+  return (uint16_t)((exp_field << 10) | (qi - 1024));
+}
+uint16_t half_down(double v) {
+  if (v == 0.0) return 0x0000u;
+  return v > 0 ? half_pos(v, false) : (uint16_t)(0x8000u | half_pos(-v, true));
+}
+uint16_t half_up(double v) {
+  if (v == 0.0) return 0x0000u;
+  return v > 0 ? half_pos(v, true) : (uint16_t)(0x8000u | half_pos(-v, false));
+}
+
 }  // namespace
 
 extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_t *tris_host, int64_t n_tris, int k,
@@ -207,8 +239,8 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   if (k != 6 && k != 18 && k != 24 && k != 26) return cbvh::fail(CBVH_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (branching != 2 && branching != 4 && branching != 8 && branching != 16)
     return cbvh::fail(CBVH_ERR_ARG, "branching must be 2, 4, 8 or 16");
-  if (quant_bits != 0 && quant_bits != 8 && quant_bits != 16)
-    return cbvh::fail(CBVH_ERR_ARG, "quant_bits must be 0, 8 or 16");
+  if (quant_bits != 0 && quant_bits != CBVH_QUANT_FP16 && quant_bits != 8 && quant_bits != 16)
+    return cbvh::fail(CBVH_ERR_ARG, "quant_bits must be 0 (FP32), 1 (FP16), 8 or 16");
   if (treelet_bytes < 4096 || treelet_bytes > 131072 || (treelet_bytes & (treelet_bytes - 1)))
     return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes must be a power of two in [4096, 131072]");
   if (n_tris < 1 || n_tris > 0x7fffffff || n_verts < 3 || n_verts > 0x7fffffff)
@@ -221,8 +253,12 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   h->bits = quant_bits;
   h->treelet_bytes = treelet_bytes;
   const int K = h->K;
-  h->root_bytes = 8 + 8 * K;
-  h->rec_bytes = quant_bits == 0 ? h->root_bytes : (8 + 2 * K * (quant_bits / 8) + 3) / 4 * 4;
+  if (quant_bits == CBVH_QUANT_FP16) {  // absolute half-precision bounds in every record
+    h->root_bytes = h->rec_bytes = 8 + 4 * K;
+  } else {
+    h->root_bytes = 8 + 8 * K;
+    h->rec_bytes = quant_bits == 0 ? h->root_bytes : (8 + 2 * K * (quant_bits / 8) + 3) / 4 * 4;
+  }
   if (16 + h->root_bytes + branching * h->rec_bytes > treelet_bytes) {
     delete h;
     return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes too small for one sibling group");
@@ -330,6 +366,12 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
     }
   }
   for (const Node &nd : B.nodes) h->depth = std::max(h->depth, nd.depth);
+  if (quant_bits == CBVH_QUANT_FP16)  // every bound lies inside the root's: check the root
+    for (int j = 0; j < 2 * K; ++j)
+      if (std::fabs(std::ldexp((double)lat[j], h->e)) > 65504.0) {
+        delete h;
+        return cbvh::fail(CBVH_ERR_MESH, "mesh bounds exceed the half-precision range (+-65504) of quant_bits = 1");
+      }
 
   // ---- treelets ----
   std::vector<int32_t> tlet(nn), local(nn), child_tlet(nn, -1);
@@ -423,7 +465,7 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   for (int64_t x = 0; x < nn; ++x) {
     const int32_t *C = &lat[(size_t)x * K * 2];
     int32_t *D = &dec[(size_t)x * K * 2];
-    if (local[x] == 0 || quant_bits == 0) {
+    if (local[x] == 0 || quant_bits == 0 || quant_bits == CBVH_QUANT_FP16) {
       std::copy(C, C + 2 * K, D);
       continue;
     }
@@ -487,6 +529,9 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
         if (quant_bits == 0) {
           w32(b, R + 8 + 8 * j, f32_bits(to_f32_down(D[2 * j], h->e)));
           w32(b, R + 12 + 8 * j, f32_bits(to_f32_up(D[2 * j + 1], h->e)));
+        } else if (quant_bits == CBVH_QUANT_FP16) {  // exact lattice values, rounded outward to half
+          w16(b, R + 8 + 4 * j, half_down(std::ldexp((double)D[2 * j], h->e)));
+          w16(b, R + 10 + 4 * j, half_up(std::ldexp((double)D[2 * j + 1], h->e)));
         } else if (l == 0) {
           w32(b, R + 8 + 8 * j, (uint32_t)D[2 * j]);
           w32(b, R + 12 + 8 * j, (uint32_t)D[2 * j + 1]);

@@ -23,6 +23,7 @@
 // intrinsics) and the interval is widened by a bound on the rounding error of u_j, so a
 // pair is pruned only if its exact bounding volumes are disjoint.  PQ uses the same
 // intervals for the slab-gap lower bound max_j gap_j / |d_j|.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,7 +80,7 @@ struct Layout {
   int o_pose;
   int o_tagA, o_latA, o_pathA;
   int o_tagB, o_latB, o_pathB;
-  int o_aset, o_bset, o_bvd;
+  int o_aset, o_bset, o_bvd, o_shift;
   int KS;  // row stride (floats) of the per-child direction arrays
 };
 
@@ -154,14 +155,38 @@ __device__ __forceinline__ int2 apply_delta(int2 P, const uint8_t *r, int bits, 
   int s = max(0, (32 - __clz((int)range)) - bits);
   return make_int2((int)((uint32_t)P.x + (dl << s)), (int)((uint32_t)P.y - (dh << s)));
 }
+// Shift of the correctors of a child whose parent's decoded interval is P.
+__device__ __forceinline__ int delta_shift(int2 P, int bits) {
+  const uint32_t range = (uint32_t)P.y - (uint32_t)P.x;
+  return max(0, (32 - __clz((int)range)) - bits);
+}
+// apply_delta with the shift already known (it depends on the parent only).
+__device__ __forceinline__ int2 apply_delta_s(int2 P, const uint8_t *r, int bits, int j, int s) {
+  uint32_t dl, dh;
+  if (bits == 8) {
+    const uint32_t v = *reinterpret_cast<const uint16_t *>(r + 8 + 2 * j);
+    dl = v & 0xffu;
+    dh = v >> 8;
+  } else {
+    const uint32_t v = ld32(r + 8 + 4 * j);
+    dl = v & 0xffffu;
+    dh = v >> 16;
+  }
+  return make_int2((int)((uint32_t)P.x + (dl << s)), (int)((uint32_t)P.y - (dh << s)));
+}
 __device__ __forceinline__ int2 abs_lattice(const uint8_t *r, int j) {
   return *reinterpret_cast<const int2 *>(r + 8 + 8 * j);
 }
 __device__ __forceinline__ float2 lat_to_f(int2 L, float scale) {
   return make_float2(__fmul_rn(__int2float_rd(L.x), scale), __fmul_rn(__int2float_ru(L.y), scale));
 }
-__device__ __forceinline__ float2 abs_float(const uint8_t *r, int j) {
-  return *reinterpret_cast<const float2 *>(r + 8 + 8 * j);
+// Absolute bounds (lo, hi) of direction j in a record of an FP32 (bits 0) or FP16 (bits 1)
+// hierarchy; half to float conversion is exact.
+__device__ __forceinline__ float2 abs_bound(const uint8_t *r, int j, int bits) {
+  if (bits == 0) return *reinterpret_cast<const float2 *>(r + 8 + 8 * j);
+  const uint32_t v = ld32(r + 8 + 4 * j);  // lo in the low half, hi in the high half
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(v & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(v >> 16))));
 }
 
 // Warp-side decode cache of one BVH: per depth below a treelet root, the reference and the
@@ -193,14 +218,11 @@ __device__ __forceinline__ const uint8_t *tbase(const BVd &X, const Side &S, uin
 // Decoded lattice interval of node x for direction j (lanes j < nd).  Walks up to the
 // deepest cached ancestor (or the treelet root), then applies the correctors down to x,
 // refreshing the cache on the way.  Returns x's record; all lanes must call it.
-__device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int lane, int2 &P) {
+// w0: the first word of x's record (the caller has it); S.cur_t / cur_base must hold x's
+// treelet.
+__device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, int lane, int2 &P) {
   const uint32_t t = x >> X.lbits, l = x & X.lmask;
-  if (t != S.cur_t) {
-    S.cur_t = t;
-    S.cur_base = tbase(X, S, t);
-  }
-  const uint8_t *rx = rec_at(X, S.cur_base, l);
-  uint32_t w = ld32(rx);
+  uint32_t w = w0;
   const int d = (int)(w >> 24);
   int dd = d, start = -1;
   uint32_t ll = l;
@@ -212,9 +234,13 @@ __device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int la
     }
     if (lane == 0) S.path[dd] = (int)ll;
     if (dd == 0) break;
-    ll = w & 0xffffu;
-    w = ld32(rec_at(X, S.cur_base, ll));
+    ll = w & 0xffffu;  // the parent: in depth-first order usually cached, so look before loading
     --dd;
+    if (S.tag[dd] == (tb | ll)) {
+      start = dd;
+      break;
+    }
+    w = ld32(rec_at(X, S.cur_base, ll));  // not cached: its record leads one level up
   }
   __syncwarp();
   const bool act = lane < S.nd;
@@ -237,7 +263,6 @@ __device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int la
     if (lane == 0) S.tag[lev] = tb | pl;
   }
   __syncwarp();
-  return rx;
 }
 
 // Decode the set that Algorithm 1 expands for node x -- its children, or x itself when x is
@@ -247,7 +272,7 @@ __device__ const uint8_t *chain_decode(const BVd &X, Side &S, uint32_t x, int la
 // the number of members (warp-uniform).
 template <int ND>
 __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float2 *iv, int KS,
-                          uint32_t *ref, uint32_t *leaf, bool leaf_bounds = true) {
+                          uint32_t *ref, uint32_t *leaf, int *shift, bool leaf_bounds = true) {
   const uint32_t t = x >> X.lbits;
   if (t != S.cur_t) {
     S.cur_t = t;
@@ -267,9 +292,9 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     __syncwarp();
     return 1;
   }
-  if (X.bits == 0) {
+  if (X.bits <= 1) {  // absolute bounds in every record
     if (self) {
-      if (lane < nd) iv[lane] = abs_float(rx, lane);
+      if (lane < nd) iv[lane] = abs_bound(rx, lane, X.bits);
       if (lane == 0) {
         ref[0] = x;
         leaf[0] = nc == 0 ? w1 : 0xffffffffu;
@@ -286,7 +311,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
           cref = (t << X.lbits) | (w1 + i);
           rc = rec_at(X, S.cur_base, w1 + i);
         }
-        iv[i * KS + j] = abs_float(rc, j);
+        iv[i * KS + j] = abs_bound(rc, j, X.bits);
         if (j == 0) {
           const uint32_t cw0 = ld32(rc);
           ref[i] = cref;
@@ -299,7 +324,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
   }
   if (self || !ext) {
     int2 P;
-    chain_decode(X, S, x, lane, P);
+    chain_decode(X, S, x, w0, lane, P);
     if (self) {
       if (lane < nd) iv[lane] = lat_to_f(P, X.scale);
       if (lane == 0) {
@@ -311,6 +336,10 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     }
   }
   const int d = (int)(w0 >> 24);
+  if (!ext) {  // the children's corrector shifts, one per direction
+    if (lane < nd) shift[lane] = delta_shift(S.lat[d * nd + lane], X.bits);
+    __syncwarp();
+  }
   for (int it = lane; it < nc * nd; it += 32) {
     const int i = it / nd, j = it - i * nd;
     const uint8_t *rc;
@@ -323,7 +352,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     } else {
       cref = (t << X.lbits) | (w1 + i);
       rc = rec_at(X, S.cur_base, w1 + i);
-      L = apply_delta(S.lat[d * nd + j], rc, X.bits, j);
+      L = apply_delta_s(S.lat[d * nd + j], rc, X.bits, j, shift[j]);
     }
     iv[i * KS + j] = lat_to_f(L, X.scale);
     if (j == 0) {
@@ -694,6 +723,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
   float2 *piv = reinterpret_cast<float2 *>(bhm + kMaxM);      // B members projected on A's directions [i][KS]
   uint32_t *bref = reinterpret_cast<uint32_t *>(piv + kMaxM * KS);
   uint32_t *bleaf = bref + kMaxM;
+  int *shift = reinterpret_cast<int *>(ws + p.L.o_shift);
   for (int i = lane; i <= p.L.tdA; i += 32) SA.tag[i] = 0xffffffffu;
   for (int i = lane; i <= p.L.tdB; i += 32) SB.tag[i] = 0xffffffffu;
   __syncwarp();
@@ -925,14 +955,14 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       // order one of them is often the same as in the previous expansion and is reused.
       int na, nb;
       if (a != keyA || root) {
-        na = decode_set<KA>(A, SA, a, root, lane, aiv, KS, aref, aleaf);
+        na = decode_set<KA>(A, SA, a, root, lane, aiv, KS, aref, aleaf, shift);
         keyA = root ? 0xffffffffu : a;
         na_c = na;
       } else {
         na = na_c;
       }
       if (b != keyB || root) {
-        nb = decode_set<3>(B, SB, b, root, lane, bvv, 4, bref, bleaf, false);
+        nb = decode_set<3>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
         if (lane < nb && bleaf[lane] == 0xffffffffu) member_box(bvv, lane, bcm[lane], bhm[lane]);
         __syncwarp();
         for (int it = lane; it < nb * KA; it += 32) {
@@ -1309,8 +1339,8 @@ __global__ void decode_all_kernel(const BVd X, int32_t *lat_out, float *f_out) {
     const uint32_t l = it / X.K, j = it - l * X.K;
     const uint8_t *r = rec_at(X, tb, l);
     float2 f;
-    if (X.bits == 0) {
-      f = abs_float(r, j);
+    if (X.bits <= 1) {
+      f = abs_bound(r, j, X.bits);
     } else {
       uint32_t path[64];
       int d = 0;
@@ -1391,6 +1421,8 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   o = align16(o + 4 * (2 * kMaxM * 4 + 8 * kMaxM + 2 * kMaxM * L.KS + 2 * kMaxM));
   L.o_bvd = o;
   o = align16(o + 2 * (int)sizeof(BVd));
+  L.o_shift = o;  // corrector shifts of the set being decoded, one per direction
+  o = align16(o + 4 * kMaxK);
   L.warp_bytes = o;
   return L;
 }

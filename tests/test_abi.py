@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(cb):
 
 
 CONFIGS = [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096), (26, 16, 16, 8192), (18, 4, 0, 4096),
-           (24, 8, 16, 65536), (18, 2, 16, 131072), (18, 16, 8, 32768)]
+           (24, 8, 16, 65536), (18, 2, 16, 131072), (18, 16, 8, 32768), (18, 4, 1, 4096), (26, 8, 1, 16384)]
 
 
 @pytest.fixture(params=[0, 1], ids=["top_down", "bottom_up"])
@@ -64,7 +64,13 @@ def test_blob_identical_to_oracle_terrain_and_odd_meshes(cb, packing):
                  (np.array([[0, 0, 0], [1e-3, 0, 0], [0, 2e-3, 1e-4]], np.float32), np.array([[0, 1, 2]], np.int32)),
                  (np.array([[1e6, 1e6, 1e6], [1e6 + 64, 1e6, 1e6], [1e6, 1e6 + 64, 1e6 - 32]], np.float32),
                   np.array([[0, 1, 2]], np.int32))]:
-        for k, m, bits, tb in [(24, 8, 8, 16384), (18, 4, 16, 4096)]:
+        for k, m, bits, tb in [(24, 8, 8, 16384), (18, 4, 16, 4096), (18, 4, 1, 4096)]:
+            if bits == 1 and np.abs(v).max() > 60000:  # beyond half precision: both refuse
+                with pytest.raises(oracle.OracleError):
+                    oracle.BVH(v, t, k, m, bits, tb, packing=packing)
+                with pytest.raises(cb.CbvhError):
+                    cb.BVH(v, t, k, m, bits, tb, device=None)
+                continue
             o = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
             h = cb.BVH(v, t, k, m, bits, tb, device=None)
             assert (o.blob() == h.blob_host()).all()

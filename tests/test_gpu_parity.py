@@ -61,7 +61,8 @@ def bottom_up(cb):
 
 @pytest.mark.parametrize("packing", [0, 1])
 @pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
-                                         (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536)])
+                                         (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536),
+                                         (18, 4, 1, 4096), (24, 8, 1, 16384)])
 def test_decode_bit_exact(cb, k, m, bits, tb, packing):
     v, t = synth.icosphere(4, 1.0, 0.15, seed=40 + k)
     cb.set_option(cb.OPT_TREELET_PACKING, packing)
@@ -72,7 +73,7 @@ def test_decode_bit_exact(cb, k, m, bits, tb, packing):
     lat, f = h.decode_all()
     o_lat, o_f, _ = oracle.decode_blob(h.blob_host())
     assert (f.cpu().numpy().view(np.uint32) == o_f.view(np.uint32)).all()
-    if bits:
+    if bits >= 8:
         assert (lat.cpu().numpy() == o_lat).all()
 
 
@@ -136,7 +137,8 @@ def test_brute_force_agrees_on_a_c1_subset(cb, c1):
 
 
 @pytest.mark.parametrize("k,m,bits,tb", [(6, 2, 8, 4096), (18, 4, 0, 4096), (18, 4, 8, 4096), (24, 8, 16, 16384),
-                                         (26, 16, 16, 8192), (24, 16, 8, 131072), (18, 2, 16, 65536)])
+                                         (26, 16, 16, 8192), (24, 16, 8, 131072), (18, 2, 16, 65536),
+                                         (18, 4, 1, 4096), (24, 8, 1, 16384)])
 def test_other_configs_bit_exact(cb, c1, k, m, bits, tb):
     va, ta, vb, tb_ = c1["mesh"]
     A = cb.BVH(va, ta, k, m, bits, tb)
@@ -236,7 +238,7 @@ def test_compressed_and_uncompressed_agree(cb, c1):
     va, ta, vb, tb_ = c1["mesh"]
     P = _gpu(c1["P"])
     res, dists = [], []
-    for bits in (0, 8, 16):
+    for bits in (0, 1, 8, 16):
         A = cb.BVH(va, ta, 18, 4, bits, 4096)
         B = cb.BVH(vb, tb_, 18, 4, bits, 4096)
         res.append(cb.collide(A, B, P))

@@ -149,7 +149,8 @@ def test_tree_split_properties(m):
 
 @pytest.mark.parametrize("packing", [oracle.PACKING_TOP_DOWN, oracle.PACKING_BOTTOM_UP])
 @pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
-                                         (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536)])
+                                         (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536),
+                                         (18, 4, 1, 4096), (24, 8, 1, 16384)])
 def test_encoding_invariants(k, m, bits, tb, packing):
     v, t = synth.icosphere(3, 1.0, 0.15, seed=5)
     h = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
@@ -162,7 +163,7 @@ def test_encoding_invariants(k, m, bits, tb, packing):
     par = tr["parent"][1:]
     assert (dec[1:, :, 0] >= dec[par, :, 0]).all() and (dec[1:, :, 1] <= dec[par, :, 1]).all()
     # correctors fit b bits
-    if bits:
+    if bits >= 8:
         assert pl["delta"].max() <= (1 << bits) - 1
     # the FP32 bounds contain the exact real bounds d.v of every vertex of the node
     e = h.e
@@ -177,7 +178,7 @@ def test_encoding_invariants(k, m, bits, tb, packing):
     # the independent decoder reproduces the encoder, node by node
     lat, f, meta = oracle.decode_blob(h.blob())
     order = np.lexsort((pl["local"], pl["treelet"]))
-    if bits:
+    if bits >= 8:
         assert (lat == dec[order]).all()
     assert (f.view(np.uint32) == decf[order].view(np.uint32)).all()
     assert ((meta[:, 0] >> 16) & 31 == tr["nchild"][order]).all()
@@ -202,6 +203,38 @@ def test_encoding_invariants(k, m, bits, tb, packing):
         # treelets are numbered in node order of their roots
         rn = np.flatnonzero(roots)
         assert (pl["treelet"][rn] == np.arange(len(rn))).all()
+
+
+def test_half_precision_rounding_is_outward_and_tight():
+    """The FP16 descriptor mode's conversion against numpy's binary16 (round to nearest):
+    the rounded-down and rounded-up halves bracket v, are adjacent (or equal when v is a
+    half), and one of them is numpy's nearest half; every non-negative bit pattern decodes
+    to numpy's value."""
+    bits = np.arange(0, 0x7c00, dtype=np.uint16)
+    ref = bits.view(np.float16).astype(np.float64)
+    for b in list(range(0, 0x7c00, 97)) + [0x0001, 0x03ff, 0x0400, 0x3c00, 0x7bff]:
+        assert oracle.half_value(b) == ref[b]
+        assert oracle.half_value(0x8000 | b) == -ref[b]
+    assert oracle.half_value(0x7c00) == np.inf
+    rng = np.random.default_rng(17)
+    vals = np.concatenate([rng.uniform(-1, 1, 200) * 10.0 ** rng.integers(-9, 5, 200),
+                           [0.0, 1.0, -1.0, 65504.0, 65504.5, -70000.0, 1e-9, -3e-8, 2.0 ** -24, 0.1]])
+    for v in vals:
+        lo, hi = oracle.half_rd(v), oracle.half_ru(v)
+        vl, vh = oracle.half_value(lo), oracle.half_value(hi)
+        assert vl <= v <= vh
+        if abs(v) <= 65504.0:
+            nearest = float(np.float16(v))
+            assert nearest in (vl, vh)
+            if v > 0:
+                assert hi - lo in (0, 1)
+            elif v < 0:
+                assert (lo & 0x7fff) - (hi & 0x7fff) in (0, 1)
+            if nearest == v:
+                assert vl == vh == v
+    assert oracle.half_value(oracle.half_ru(70000.0)) == np.inf
+    assert oracle.half_value(oracle.half_rd(70000.0)) == 65504.0
+    assert oracle.half_value(oracle.half_rd(-70000.0)) == -np.inf
 
 
 def test_bad_arguments_and_meshes():
