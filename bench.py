@@ -71,11 +71,33 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def rank_poses(n_poses: int, rank: int, height_fn):
+    """Weak scaling: every rank gets its own poses of the terrain distribution (rank 0 the
+    workload's own, seed 2002; rank r seed 2002 + 7919 r).  No data-path collective."""
+    return synth.poses_terrain(n_poses, seed=2002 + 7919 * rank, height_fn=height_fn)
+
+
 def workload(n_poses: int, rank: int):
     c = synth.C2(n_poses)
-    if rank:  # weak scaling: every rank gets its own poses of the same distribution
-        c["poses"] = synth.poses_terrain(n_poses, seed=2002 + 7919 * rank, height_fn=c["height"])
+    if rank:
+        c["poses"] = rank_poses(n_poses, rank, c["height"])
     return c
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's value (all ranks get it); x itself with one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Units of all ranks per second of the slowest rank."""
+    return units_per_rank * world / (max_ms / 1e3)
 
 
 # ------------------------------------------------------------------ CPU (oracle) timing
@@ -555,6 +577,7 @@ def main():
     torch.cuda.synchronize()
     cb.profile_collect()
     cb.profile_enable(True)
+    launches0 = cb.kernel_launches()
     with ClockSampler(uuid or None) as clk:
         for s in range(K):
             flush.zero_()
@@ -562,21 +585,15 @@ def main():
             step(poses)
             ev[s][1].record(stream)
         torch.cuda.synchronize()
+    gpu_launches = cb.kernel_launches() - launches0  # the library's own count, timed region only
     cb.profile_enable(False)
     prof = cb.profile_collect()
-    # our kernels per step: the traversal rounds of collide, its compaction (scan, scatter,
-    # sort), and the two traversal passes of distance
-    kernel_launches_cd = 6 + 3
-    kernel_launches_pq = 2 * 6
+
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = 2 * n * K * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = whole_job_rate(2 * n * K, world, total_ms)
 
     # ---- end to end: pinned host poses in, results out, every step ----
     hit_h = torch.empty(n, dtype=torch.uint8).pin_memory()
@@ -585,6 +602,8 @@ def main():
     dist_h = torch.empty(n, dtype=torch.float32).pin_memory()
     poses_e = torch.empty_like(poses)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     for s in range(K):
@@ -596,8 +615,8 @@ def main():
         dist_h.copy_(dist_out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_val = 2 * n * K * world / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    e2e_val = whole_job_rate(2 * n * K, world, e2e_ms)
     h2d = n * 48
     d2h = n * 1 + (n + 1) * 8 + n_pairs * 8 + n * 4
 
@@ -651,7 +670,7 @@ def main():
         torch.cuda.empty_cache()
         extra["scale"] = scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses, args.scale_pair_poses)
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         rate, done, secs, cores = oracle_rate(c, args.cpu_sample)
         cpu = {"value": rate, "unit": "pose queries/s", "cores": cores, "kind": "oracle",
                "sample": f"first {done} poses of the 10,000-pose set, CD with pairs + PQ, {secs:.1f} s"}
@@ -683,7 +702,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "pose queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
-        "gpu_launches": K * (kernel_launches_cd + kernel_launches_pq),
+        "gpu_launches": gpu_launches,
     }
     out.update(extra)
     print(json.dumps(out), flush=True)

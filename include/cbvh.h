@@ -222,6 +222,11 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
 #define CBVH_PACK_BOTTOM_UP 1
 int cbvh_set_option(int option, int64_t value);
 
+/* Kernels this library has launched in this process so far (every traversal round, every
+ * compaction kernel, the decode hook); a count the caller can difference around a region.
+ * Host only; no synchronisation.  Errors: CBVH_ERR_ARG (NULL). */
+int cbvh_kernel_launches(int64_t *count);
+
 /* Work counters of the last query that used `workspace`: stats_host[0] = BV-pair tests
  * (bounding-volume overlap or lower-bound tests, Algorithm 1's "a and b intersect"),
  * stats_host[1] = leaf tests (checkPrimitives calls), stats_host[2] = node-pair expansions

@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
-           "set_option", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
+           "set_option", "kernel_launches", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
            "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "SPLIT_POSE", "SPLIT_ROUNDS", "SPLIT_QUEUE", "SPLIT_ROUNDS_QUEUE", "SPLIT_AUTO",
            "SPLIT_DEFAULT", "BUDGET0_DEFAULT", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
@@ -60,10 +60,12 @@ def _declare(L):
     L.cbvh_set_option.argtypes = [I32, I64]
     L.cbvh_profile_enable.argtypes = [I32]
     L.cbvh_profile_collect.argtypes = [P, P]
+    L.cbvh_kernel_launches.argtypes = [C.POINTER(I64)]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
               "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
               "cbvh_profile_collect", "cbvh_distance_noalloc", "cbvh_batch_create", "cbvh_batch_free",
-              "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option"):
+              "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option",
+              "cbvh_kernel_launches"):
         getattr(L, f).restype = I32
     return L
 
@@ -178,6 +180,13 @@ PACK_TOP_DOWN, PACK_BOTTOM_UP = 0, 1
 SPLIT_POSE, SPLIT_ROUNDS, SPLIT_QUEUE, SPLIT_ROUNDS_QUEUE, SPLIT_AUTO = 0, 1, 2, 3, 4
 SPLIT_DEFAULT = SPLIT_AUTO
 BUDGET0_DEFAULT = 256
+
+
+def kernel_launches() -> int:
+    """cbvh_kernel_launches: kernels the library has launched in this process so far."""
+    out = C.c_int64()
+    _check(_load().cbvh_kernel_launches(C.byref(out)))
+    return out.value
 
 
 def set_option(option: int, value: int) -> None:

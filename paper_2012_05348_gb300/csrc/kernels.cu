@@ -1383,6 +1383,7 @@ int align16(int x) { return (x + 15) & ~15; }
 // Process-wide tuning options (cbvh_set_option).
 std::atomic<int> g_stage_bytes{kStageBytesDefault};
 std::atomic<int> g_split{4};  // work mapping, see launch_rounds
+std::atomic<long long> g_launches{0};  // kernels this library has launched (cbvh_kernel_launches)
 std::atomic<int> g_budget0{256};  // expansion budget of a task in round 0 (later rounds scale it)
 
 // Per-warp slice layout for A's direction count, the deepest nodes below a treelet root on
@@ -1622,6 +1623,7 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint32
       if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     }
     fn<<<blocks, kThreads, smem, s>>>(p);
+    g_launches.fetch_add(1);
   }
   e = cudaGetLastError();
   if (g_prof.on) {
@@ -1685,6 +1687,7 @@ extern "C" int cbvh_decode_all(const cbvh_bvh *h, int32_t *lattice_out, float *b
   if (!h->dev_blob) return cbvh::fail(CBVH_ERR_STATE, "handle has no device blob; call cbvh_attach");
   decode_all_kernel<<<(unsigned)h->n_treelets, 128, 0, static_cast<cudaStream_t>(stream)>>>(view(h), lattice_out,
                                                                                              bounds_out);
+  g_launches.fetch_add(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "decode launch");
 }
@@ -1762,8 +1765,11 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
     }
     scan_kernel<<<1, 1024, 0, s>>>(counts, n, pair_offsets, pairs_needed, p.cap, status);
     scatter_kernel<<<1024, 256, 0, s>>>(triples, p.pair_count, p.cap, pair_offsets, counts, pairs);
-    if (flags & CBVH_SORT_PAIRS)
+    g_launches.fetch_add(2);
+    if (flags & CBVH_SORT_PAIRS) {
       sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(pair_offsets, n, p.pair_count, p.cap, pairs);
+      g_launches.fetch_add(1);
+    }
     e = cudaGetLastError();
     if (g_prof.on) {
       cudaEventRecord(rec.b, s);
@@ -1938,6 +1944,7 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
     p.tasks_in = buf[(r + 1) & 1];
     p.tasks_out = buf[r & 1];
     fn<<<blocks, kThreads, smem, s>>>(p);
+    g_launches.fetch_add(1);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "traverse launch");
@@ -2152,6 +2159,13 @@ extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t w
       if (int rc = launch_rounds<MODE_PQ>(p, ctr + 32, t0, t1, rdy, st, b->task_cap, b->sms, s)) return rc;
     }
   }
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_kernel_launches(int64_t *count) {
+  cbvh::clear_error();
+  if (!count) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  *count = g_launches.load();
   return CBVH_OK;
 }
 

@@ -133,3 +133,10 @@ def test_batch_rejects_unattached_handles(cb):
     assert cb.lib.cbvh_set_option(cb.OPT_STAGE_BYTES, 1 << 20) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_TREELET_PACKING, 2) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_SPLIT, 5) == -1
+
+
+def test_kernel_launch_counter_without_gpu(cb):
+    """The counter is host state: readable without a device, and NULL is an argument error."""
+    n = cb.kernel_launches()
+    assert n >= 0 and cb.kernel_launches() == n
+    assert cb.lib.cbvh_kernel_launches(None) == -1

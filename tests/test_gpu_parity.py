@@ -353,3 +353,16 @@ def test_bottom_up_terrain_equals_top_down(cb, c2):
     assert torch.equal(r0.hit, r1.hit) and torch.equal(r0.offsets, r1.offsets) and torch.equal(r0.pairs, r1.pairs)
     d0, d1 = cb.distance(c2["A"], c2["B"], P).cpu().numpy(), cb.distance(A, c2["B"], P).cpu().numpy()
     assert np.abs(d0 - d1).max() <= 1e-6 * c2["D"]
+
+
+def test_kernel_launch_counter(cb, c1):
+    """cbvh_kernel_launches counts what a query launches: with the default mapping a collide
+    with sorted pair lists is one work-queue traversal + scan, scatter and sort; a distance
+    is six rounds of early-exit collision and six of branch and bound."""
+    P = _gpu(c1["P"])
+    n0 = cb.kernel_launches()
+    cb.collide(c1["A"], c1["B"], P, capacity=1 << 20)
+    n1 = cb.kernel_launches()
+    cb.distance(c1["A"], c1["B"], P)
+    n2 = cb.kernel_launches()
+    assert n1 - n0 == 4 and n2 - n1 == 12
