@@ -11,8 +11,9 @@ Metric: pose queries/s, a CD query and a PQ query of one pose counting as two.
 Prints one JSON line (rank 0).  After the timed headline step the same line carries the
 comparisons of `--sections`: the batched arm sweep against one query per link and launch,
 the served request loop against one call per request, the terrain step under every way
-of storing the bounds (8/16-bit deltas, FP16, FP32), and the scale-and-compression
-workload (a 10M-triangle field that does not fit in L2) at every compression setting.
+of storing the bounds (8/16-bit deltas, FP16, FP32), the device refit of a deforming mesh
+(terrain and 10M-triangle field), and the scale-and-compression workload (a 10M-triangle
+field that does not fit in L2) at every compression setting.
 `--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the same
 poses; `--scale-only` runs just the scale comparison (an entry point for profiling).
 """
@@ -56,9 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
     ap.add_argument("--arm-configs", type=int, default=200000)
-    ap.add_argument("--sections", default="batched,served,compression,scale",
-                    help="comparisons run after the headline step: batched, served, compression, scale "
-                         "(comma list)")
+    ap.add_argument("--sections", default="batched,served,compression,refit,scale",
+                    help="comparisons run after the headline step: batched, served, compression, refit, "
+                         "scale (comma list)")
     ap.add_argument("--scale-poses", type=int, default=1_000_000)
     ap.add_argument("--scale-pq-poses", type=int, default=20_000)
     ap.add_argument("--scale-pair-poses", type=int, default=100_000)
@@ -260,6 +261,15 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
             batch.launch()
         ms_batched = _events_ms(g.replay, torch)
         collide_cfg = np.stack([o.cpu().numpy() for o in outs]).any(0)
+        # self-collision: every non-adjacent link pair, link j posed in link i's frame
+        sp = synth.self_pairs(6)
+        rel = [torch.as_tensor(synth.relative_poses(c["link_poses"], i, j), device=dev) for i, j in sp]
+        self_items = [dict(A=links[i], B=links[j], kind="collide", poses=R, early_exit=True)
+                      for (i, j), R in zip(sp, rel)]
+        self_batch = cb.Batch(self_items, device=dev)
+        self_outs = self_batch.run()
+        ms_self = _events_ms(self_batch.run, torch)
+        self_cfg = np.stack([o.cpu().numpy() for o in self_outs]).any(0)
 
         def plain():
             for L, P in zip(links, LP):
@@ -274,6 +284,10 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
             "autotuned": {"best": best, "sample_configurations": tune_configs, "candidates": len(trials),
                           "tuning_s": tune_s, "sample_ms_best": best_ms, "sample_ms_default": default_ms},
             "link_queries": q, "configs_in_collision": int(collide_cfg.sum()),
+            "self_collision": {"link_pairs": len(sp), "pair_queries": len(sp) * n_configs,
+                               "configs_self_colliding": int(self_cfg.sum()), "ms": ms_self,
+                               "pair_queries_per_s": len(sp) * n_configs / (ms_self / 1e3)},
+            "configs_free": int((~collide_cfg & ~self_cfg).sum()),
             "batched_link_queries_per_s": q / (ms_batched / 1e3), "batched_ms": ms_batched,
             "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,
             "speedup_vs_plain": ms_plain / ms_batched,
@@ -400,6 +414,38 @@ def compression(cb, torch, dev, c, steps=3):
         torch.cuda.empty_cache()
     return {"workload": "terrain step (10,000 poses, CD with sorted pairs + PQ), 24-DOP, branching 8, 16 KB treelets",
             "modes": out}
+
+
+def refit_rate(cb, torch, dev, verts, tris, k, m, bits, tb, packing, reps=5):
+    """Device refit (deforming meshes) of one hierarchy: the mesh breathes (every vertex
+    scaled about the origin by 1 +- 0.1 %), the tree is kept and every bound recomputed and
+    re-encoded on the GPU.  Algorithmic bytes: per triangle its index, three vertex indices,
+    three vertices in and the triangle out (88 B); per node the plan (24 B), the exact
+    bounds written, merged and read back and the decoded bounds (24 B per direction) and its
+    record."""
+    cb.set_option(cb.OPT_TREELET_PACKING, packing)
+    cb.set_option(cb.OPT_LATTICE_HEADROOM, 1)  # room for the larger breath
+    try:
+        h = cb.BVH(verts, tris, k, m, bits, tb, device=dev)
+    finally:
+        cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
+        cb.set_option(cb.OPT_LATTICE_HEADROOM, 0)
+    T = torch.as_tensor(tris, device=dev)
+    V = [torch.as_tensor((verts * s).astype(np.float32), device=dev) for s in (1.001, 0.999)]
+    h.refit(V[0], T)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(reps):
+        h.refit(V[r & 1], T, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nn, nt = h.info["n_nodes"], h.info["n_tris"]
+    rec = 8 + (4 * k // 2 if bits == 1 else (8 * k // 2 if bits == 0 else k * bits // 8))
+    algo = nt * 88 + nn * (24 + 24 * (k // 2) + rec)
+    return {"triangles": nt, "nodes": nn, "quant_bits": bits, "ms": ms, "triangles_per_s": nt / (ms / 1e3),
+            "algorithmic_gbs": algo / (ms * 1e6)}
 
 
 def _bv_bytes(k: int, bits: int) -> int:
@@ -666,6 +712,13 @@ def main():
         del models
     if "compression" in sections:
         extra["compression"] = compression(cb, torch, dev, c)
+    if "refit" in sections:
+        extra["refit"] = {"terrain": refit_rate(cb, torch, dev, c["A"][0], c["A"][1], K_DOP, BRANCH, BITS, TREELET,
+                                                cb.PACK_TOP_DOWN)}
+        c5 = synth.C5(1)
+        extra["refit"]["field10m"] = refit_rate(cb, torch, dev, c5["A"][0], c5["A"][1], 18, 4, 8, 16384,
+                                                cb.PACK_BOTTOM_UP)
+        del c5
     if "scale" in sections:
         torch.cuda.empty_cache()
         extra["scale"] = scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses, args.scale_pair_poses)

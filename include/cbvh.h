@@ -218,9 +218,41 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
  *     nodes its children still carry fit one treelet; otherwise each child roots a treelet.
  *     Fewer, fuller treelets and fewer absolute roots; deeper chains below a root. */
 #define CBVH_OPT_TREELET_PACKING 4
+/*   CBVH_OPT_LATTICE_HEADROOM: bits of the lattice range cbvh_build keeps free, 0..8
+ *   (default 0): the lattice step 2^e is the smallest with every |bound| / 2^e below
+ *   2^(30 - headroom) instead of 2^30.  cbvh_refit keeps e and accepts bounds up to 2^30
+ *   steps, so a hierarchy built with headroom h can be refitted to a mesh up to 2^h times
+ *   larger; each bit costs one bit of lattice resolution.  Takes effect for builds started
+ *   afterwards. */
+#define CBVH_OPT_LATTICE_HEADROOM 5
 #define CBVH_PACK_TOP_DOWN 0
 #define CBVH_PACK_BOTTOM_UP 1
 int cbvh_set_option(int option, int64_t value);
+
+/* ---- device refit for deforming meshes (the tree is kept, the bounds recomputed) ----
+ * New positions for the build's vertices (same count, same triangles): every node's exact
+ * lattice bounds are recomputed from them on the device and the attached blob's bound
+ * fields and triangle table are rewritten in place.  The tree, the treelets and the
+ * lattice exponent stay those of the build, so the blob is byte-identical to encoding the
+ * build's tree with the new vertices (the host copy from cbvh_blob_host is not updated).
+ * A deformation that reorders the median splits leaves the tree valid but less tight;
+ * rebuild when it matters.
+ *   cbvh_refit_workspace_bytes: device bytes of the plan and scratch (about 24 B per node
+ *     + 16 B per node and direction).
+ *   cbvh_refit_prepare: writes the node plan into `workspace` (256-byte aligned, caller-
+ *     owned, kept unchanged between refits) and synchronises `stream`; once per handle and
+ *     workspace.
+ *   cbvh_refit: verts_dev n_verts x 3 FP32 and tris_dev n_tris x 3 int32 (the build's
+ *     triangles), device pointers; asynchronous on `stream`, no synchronisation, so it can
+ *     be captured in a CUDA graph.  A vertex that is not finite or leaves the lattice's
+ *     range (|d.v| >= 2^30 steps), or a bound beyond +-65504 for quant_bits = 1, sets
+ *     `status` to CBVH_ERR_MESH; the blob is then unspecified until a successful refit.
+ * Errors: CBVH_ERR_ARG, CBVH_ERR_STATE (not attached, or workspace not prepared),
+ * CBVH_ERR_WORKSPACE, CBVH_ERR_CUDA. */
+int cbvh_refit_workspace_bytes(const cbvh_bvh *h, int64_t *bytes);
+int cbvh_refit_prepare(cbvh_bvh *h, void *workspace, int64_t workspace_bytes, void *stream);
+int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, const int32_t *tris_dev, void *workspace,
+               int64_t workspace_bytes, int32_t *status, void *stream);
 
 /* Kernels this library has launched in this process so far (every traversal round, every
  * compaction kernel, the decode hook); a count the caller can difference around a region.

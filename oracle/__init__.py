@@ -42,7 +42,7 @@ def lib():
         L = C.CDLL(_LIB)
         P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
         L.or_last_error.restype = C.c_char_p
-        L.or_build.argtypes = [P, I64, P, I64, I32, I32, I32, I32, I32, C.POINTER(C.c_void_p)]
+        L.or_build.argtypes = [P, I64, P, I64, I32, I32, I32, I32, I32, I32, C.POINTER(C.c_void_p)]
         L.or_build.restype = I32
         L.or_free.argtypes = [P]
         L.or_info.argtypes = [P, P]
@@ -51,6 +51,8 @@ def lib():
         L.or_tree.argtypes = [P, P, P, P, P]
         L.or_lattice.argtypes = [P, P, P, P, P]
         L.or_placement.argtypes = [P, P, P, P, P]
+        L.or_refit.argtypes = [P, P]
+        L.or_refit.restype = I32
         L.or_decode_blob.argtypes = [P, I64, P, P, P]
         L.or_decode_blob.restype = I64
         L.or_floor_sum3.argtypes = [D, D, D]
@@ -112,13 +114,14 @@ class OracleError(RuntimeError):
 class BVH:
     """The oracle's BVH of one mesh: its tree, exact lattice bounds, encoding and blob."""
 
-    def __init__(self, verts, tris, k: int, m: int, bits: int, treelet_bytes: int, packing: int = PACKING_DEFAULT):
+    def __init__(self, verts, tris, k: int, m: int, bits: int, treelet_bytes: int, packing: int = PACKING_DEFAULT,
+                 headroom: int = 0):
         L = lib()
         self.verts = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
         self.tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
         h = C.c_void_p()
         rc = L.or_build(_p(self.verts), len(self.verts), _p(self.tris), len(self.tris), k, m, bits,
-                        treelet_bytes, packing, C.byref(h))
+                        treelet_bytes, packing, headroom, C.byref(h))
         if rc != 0:
             raise OracleError(rc, L.or_last_error().decode())
         self._h = h
@@ -136,6 +139,17 @@ class BVH:
     @property
     def handle(self):
         return self._h
+
+    def refit(self, verts) -> None:
+        """New positions for the build's vertices: same tree, treelets and lattice exponent;
+        exact bounds, encoding and blob redone (or_refit)."""
+        v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+        if v.shape != self.verts.shape:
+            raise ValueError("refit needs the build's vertex count")
+        rc = lib().or_refit(self._h, _p(v))
+        if rc != 0:
+            raise OracleError(rc, lib().or_last_error().decode())
+        self.verts = v
 
     def blob(self) -> np.ndarray:
         ptr = lib().or_blob(self._h)

@@ -180,7 +180,8 @@ typedef struct {
   int32_t **tlet_nodes;
   int lbits, max_tdepth;
   int rec_bytes, root_bytes;
-  int packing; /* 0: treelets grown top-down; 1: packed bottom-up (see encode) */
+  int packing;  /* 0: treelets grown top-down; 1: packed bottom-up (see encode) */
+  int headroom; /* lattice bits kept free: e is chosen for |bound| < 2^(30 - headroom) */
   uint8_t *blob;
   int64_t blob_bytes;
 } or_bvh;
@@ -280,8 +281,9 @@ static int32_t build_rec(tbuild *b, const double *key, int32_t *ids, int64_t n) 
 
 void or_free(or_bvh *h);
 
-static int lattice_fits(const or_bvh *h, int e) {
-  const int64_t LIM = (int64_t)1 << 30;
+/* Every vertex's lattice coordinates within +-lim at exponent e. */
+static int lattice_fits(const or_bvh *h, int e, int64_t lim) {
+  const int64_t LIM = lim;
   for (int64_t t = 0; t < h->nt; ++t)
     for (int c = 0; c < 3; ++c) {
       const float *v = h->verts + 3 * (int64_t)h->tris[3 * t + c];
@@ -296,11 +298,58 @@ static int lattice_fits(const or_bvh *h, int e) {
 
 static int encode(or_bvh *h);
 
+/* Exact lattice bounds of every node (leaves from their three vertices, inner nodes as the
+ * union of their children), and the FP64 bounds of the exact coordinates. */
+static void compute_bounds(or_bvh *h) {
+  int64_t nn = h->nn;
+  int K = h->K;
+  if (!h->lat) h->lat = (int64_t *)malloc(sizeof(int64_t) * nn * K * 2);
+  if (!h->bnd) h->bnd = (double *)malloc(sizeof(double) * nn * K * 2);
+  for (int64_t i = nn - 1; i >= 0; --i) {
+    int64_t *L = h->lat + i * K * 2;
+    double *B = h->bnd + i * K * 2;
+    for (int j = 0; j < K; ++j) {
+      L[2 * j] = INT64_MAX;
+      L[2 * j + 1] = INT64_MIN;
+      B[2 * j] = INFINITY;
+      B[2 * j + 1] = -INFINITY;
+    }
+    if (h->nchild[i] == 0) {
+      int32_t t = h->tri[i];
+      for (int c = 0; c < 3; ++c) {
+        const float *v = h->verts + 3 * (int64_t)h->tris[3 * (int64_t)t + c];
+        for (int j = 0; j < K; ++j) {
+          int64_t lo, hi;
+          lattice_dv(v, j, h->e, &lo, &hi);
+          if (lo < L[2 * j]) L[2 * j] = lo;
+          if (hi > L[2 * j + 1]) L[2 * j + 1] = hi;
+          double s = OR_DIR[j][0] * (double)v[0] + OR_DIR[j][1] * (double)v[1] + OR_DIR[j][2] * (double)v[2];
+          if (s < B[2 * j]) B[2 * j] = s;
+          if (s > B[2 * j + 1]) B[2 * j + 1] = s;
+        }
+      }
+    } else {
+      for (int c = 0; c < h->nchild[i]; ++c) {
+        const int64_t *LC = h->lat + (int64_t)(h->first[i] + c) * K * 2;
+        const double *BC = h->bnd + (int64_t)(h->first[i] + c) * K * 2;
+        for (int j = 0; j < K; ++j) {
+          if (LC[2 * j] < L[2 * j]) L[2 * j] = LC[2 * j];
+          if (LC[2 * j + 1] > L[2 * j + 1]) L[2 * j + 1] = LC[2 * j + 1];
+          if (BC[2 * j] < B[2 * j]) B[2 * j] = BC[2 * j];
+          if (BC[2 * j + 1] > B[2 * j + 1]) B[2 * j + 1] = BC[2 * j + 1];
+        }
+      }
+    }
+  }
+}
+
+
 /* Build the BVH of a triangle mesh and its compressed blob. */
 int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, int k, int m, int bits,
-             int treelet_bytes, int packing, or_bvh **out) {
+             int treelet_bytes, int packing, int headroom, or_bvh **out) {
   *out = NULL;
   if (packing != 0 && packing != 1) return fail(OR_ERR_ARG, "packing must be 0 or 1");
+  if (headroom < 0 || headroom > 8) return fail(OR_ERR_ARG, "headroom must be in [0, 8]");
   if (k != 6 && k != 18 && k != 24 && k != 26) return fail(OR_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (m != 2 && m != 4 && m != 8 && m != 16) return fail(OR_ERR_ARG, "branching must be 2, 4, 8 or 16");
   if (bits != 0 && bits != 1 && bits != 8 && bits != 16)
@@ -315,6 +364,7 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   h->bits = bits;
   h->budget = treelet_bytes;
   h->packing = packing;
+  h->headroom = headroom;
   h->nv = nv;
   h->nt = nt;
   h->root_bytes = 8 + 8 * h->K;
@@ -423,8 +473,9 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
       return fail(OR_ERR_MESH, "mesh has no extent");
     }
     int e = ilogb(M) - 31;
-    while (lattice_fits(h, e)) --e; /* walk down until it no longer fits */
-    while (!lattice_fits(h, e)) ++e; /* the first one that fits */
+    const int64_t lim = (int64_t)1 << (30 - h->headroom); /* bits kept free for refits */
+    while (lattice_fits(h, e, lim)) --e;  /* walk down until it no longer fits */
+    while (!lattice_fits(h, e, lim)) ++e; /* the first one that fits */
     if (e < -120 || e > 96) {
       or_free(h);
       return fail(OR_ERR_MESH, "mesh coordinates outside the supported range");
@@ -432,46 +483,8 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
     h->e = e;
   }
 
-  /* exact lattice bounds, leaves from their three vertices, inner nodes as the union */
+  compute_bounds(h);
   int K = h->K;
-  h->lat = (int64_t *)malloc(sizeof(int64_t) * nn * K * 2);
-  h->bnd = (double *)malloc(sizeof(double) * nn * K * 2);
-  for (int64_t i = nn - 1; i >= 0; --i) {
-    int64_t *L = h->lat + i * K * 2;
-    double *B = h->bnd + i * K * 2;
-    for (int j = 0; j < K; ++j) {
-      L[2 * j] = INT64_MAX;
-      L[2 * j + 1] = INT64_MIN;
-      B[2 * j] = INFINITY;
-      B[2 * j + 1] = -INFINITY;
-    }
-    if (h->nchild[i] == 0) {
-      int32_t t = h->tri[i];
-      for (int c = 0; c < 3; ++c) {
-        const float *v = h->verts + 3 * (int64_t)h->tris[3 * (int64_t)t + c];
-        for (int j = 0; j < K; ++j) {
-          int64_t lo, hi;
-          lattice_dv(v, j, h->e, &lo, &hi);
-          if (lo < L[2 * j]) L[2 * j] = lo;
-          if (hi > L[2 * j + 1]) L[2 * j + 1] = hi;
-          double s = OR_DIR[j][0] * (double)v[0] + OR_DIR[j][1] * (double)v[1] + OR_DIR[j][2] * (double)v[2];
-          if (s < B[2 * j]) B[2 * j] = s;
-          if (s > B[2 * j + 1]) B[2 * j + 1] = s;
-        }
-      }
-    } else {
-      for (int c = 0; c < h->nchild[i]; ++c) {
-        const int64_t *LC = h->lat + (int64_t)(h->first[i] + c) * K * 2;
-        const double *BC = h->bnd + (int64_t)(h->first[i] + c) * K * 2;
-        for (int j = 0; j < K; ++j) {
-          if (LC[2 * j] < L[2 * j]) L[2 * j] = LC[2 * j];
-          if (LC[2 * j + 1] > L[2 * j + 1]) L[2 * j + 1] = LC[2 * j + 1];
-          if (BC[2 * j] < B[2 * j]) B[2 * j] = BC[2 * j];
-          if (BC[2 * j + 1] > B[2 * j + 1]) B[2 * j + 1] = BC[2 * j + 1];
-        }
-      }
-    }
-  }
   if (h->bits == 1) /* half floats: every node's bounds, hence the root's, within +-65504 */
     for (int j = 0; j < 2 * K; ++j)
       if (fabs(ldexp((double)h->lat[j], h->e)) > 65504.0) {
@@ -485,6 +498,57 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   }
   *out = h;
   return OR_OK;
+}
+
+/* Refit for deforming meshes: the same tree, treelets and lattice exponent with new
+ * positions for the build's vertices.  The exact bounds are recomputed and the encoding and
+ * blob redone.  Fails, leaving the handle as it was, when a new vertex is not finite, leaves
+ * the lattice's range, or (half floats) puts a bound beyond +-65504. */
+int or_refit(or_bvh *h, const float *verts) {
+  for (int64_t i = 0; i < 3 * h->nv; ++i)
+    if (!isfinite(verts[i])) return fail(OR_ERR_MESH, "non-finite vertex");
+  float *old = h->verts;
+  h->verts = (float *)malloc(sizeof(float) * 3 * h->nv);
+  memcpy(h->verts, verts, sizeof(float) * 3 * h->nv);
+  int ok = lattice_fits(h, h->e, (int64_t)1 << 30); /* a refit may use the headroom */
+  if (ok && h->bits == 1)
+    for (int64_t t = 0; t < h->nt && ok; ++t)
+      for (int c = 0; c < 3 && ok; ++c)
+        for (int j = 0; j < h->K && ok; ++j) {
+          int64_t lo, hi;
+          lattice_dv(h->verts + 3 * (int64_t)h->tris[3 * t + c], j, h->e, &lo, &hi);
+          if (fabs(ldexp((double)lo, h->e)) > 65504.0 || fabs(ldexp((double)hi, h->e)) > 65504.0) ok = 0;
+        }
+  if (!ok) {
+    free(h->verts);
+    h->verts = old;
+    return fail(OR_ERR_MESH, "refit: vertices outside the hierarchy's lattice or half range");
+  }
+  free(old);
+  compute_bounds(h);
+  /* drop the old encoding and redo it (treelets depend on the tree only) */
+  free(h->tlet);
+  free(h->local);
+  free(h->ext);
+  free(h->child_tlet);
+  free(h->dec);
+  free(h->delta);
+  free(h->decf);
+  free(h->tlet_root);
+  if (h->tlet_nodes)
+    for (int64_t t = 0; t < h->ntlet; ++t) free(h->tlet_nodes[t]);
+  free(h->tlet_nodes);
+  free(h->tlet_count);
+  free(h->blob);
+  h->tlet = h->local = h->child_tlet = h->tlet_root = h->tlet_count = NULL;
+  h->ext = NULL;
+  h->dec = NULL;
+  h->delta = NULL;
+  h->decf = NULL;
+  h->tlet_nodes = NULL;
+  h->blob = NULL;
+  h->ntlet = 0;
+  return encode(h);
 }
 
 /* ---- treelets and the predictor-corrector encoding ---- */

@@ -19,7 +19,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
-           "set_option", "kernel_launches", "OPT_STAGE_BYTES", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
+           "set_option", "kernel_launches", "OPT_STAGE_BYTES", "OPT_LATTICE_HEADROOM", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
            "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "SPLIT_POSE", "SPLIT_ROUNDS", "SPLIT_QUEUE", "SPLIT_ROUNDS_QUEUE", "SPLIT_AUTO",
            "SPLIT_DEFAULT", "BUDGET0_DEFAULT", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
@@ -61,11 +61,14 @@ def _declare(L):
     L.cbvh_profile_enable.argtypes = [I32]
     L.cbvh_profile_collect.argtypes = [P, P]
     L.cbvh_kernel_launches.argtypes = [C.POINTER(I64)]
+    L.cbvh_refit_workspace_bytes.argtypes = [P, C.POINTER(I64)]
+    L.cbvh_refit_prepare.argtypes = [P, P, I64, P]
+    L.cbvh_refit.argtypes = [P, P, I64, P, P, I64, P, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
               "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
               "cbvh_profile_collect", "cbvh_distance_noalloc", "cbvh_batch_create", "cbvh_batch_free",
               "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option",
-              "cbvh_kernel_launches"):
+              "cbvh_kernel_launches", "cbvh_refit_workspace_bytes", "cbvh_refit_prepare", "cbvh_refit"):
         getattr(L, f).restype = I32
     return L
 
@@ -151,6 +154,28 @@ class BVH:
         with torch.cuda.device(self.blob_dev.device):
             _check(_load().cbvh_attach(self._h, _ptr(self.blob_dev), n, _stream_ptr(stream)))
 
+    def refit(self, verts, tris, stream=None, check: bool = True):
+        """cbvh_refit (deforming meshes): new positions for the build's vertices, device
+        float32 (n_verts, 3); tris: the build's triangles, device int32 (n_tris, 3).  The
+        attached blob is rewritten in place; the plan is prepared on first use."""
+        torch = _torch()
+        if self.blob_dev is None:
+            raise CbvhError(-9, "not attached")
+        if getattr(self, "_refit_ws", None) is None:
+            nb = C.c_int64()
+            _check(_load().cbvh_refit_workspace_bytes(self._h, C.byref(nb)))
+            self._refit_ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self.blob_dev.device)
+            _check(_load().cbvh_refit_prepare(self._h, _ptr(self._refit_ws), self._refit_ws.numel(),
+                                              _stream_ptr(stream)))
+        status = torch.zeros(1, dtype=torch.int32, device=self.blob_dev.device)
+        _check(_load().cbvh_refit(self._h, _ptr(verts), int(verts.shape[0]), _ptr(tris), _ptr(self._refit_ws),
+                                  self._refit_ws.numel(), _ptr(status), _stream_ptr(stream)))
+        if check:
+            code = int(status.item())
+            if code != 0:
+                raise CbvhError(code, "device status")
+        return status
+
     def decode_all(self, stream=None):
         """(lattice int32 (n, K, 2) or None, bounds float32 (n, K, 2)) on the device, blob order."""
         torch = _torch()
@@ -174,6 +199,7 @@ OPT_STAGE_BYTES = 1
 OPT_SPLIT = 2
 OPT_BUDGET0 = 3
 OPT_TREELET_PACKING = 4
+OPT_LATTICE_HEADROOM = 5
 PACK_TOP_DOWN, PACK_BOTTOM_UP = 0, 1
 # CBVH_OPT_SPLIT values: warp per pose, rounds, work queue, rounds then work queue, and the
 # default (work queue for collision with pair lists, rounds then work queue otherwise)

@@ -24,7 +24,7 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("build.cpp", "kernels.cu", "internal.h")] + [
+    return [os.path.join(CSRC, f) for f in ("build.cpp", "kernels.cu", "refit.cu", "internal.h")] + [
         os.path.join(INCLUDE, "cbvh.h")]
 
 
@@ -42,21 +42,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     obj_host = os.path.join(BUILD_DIR, "build.o")
     obj_dev = os.path.join(BUILD_DIR, "kernels.o")
+    obj_refit = os.path.join(BUILD_DIR, "refit.o")
     host_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-I", INCLUDE, "-c",
                 os.path.join(CSRC, "build.cpp"), "-o", obj_host]
     dev_cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
                "-Xptxas", "-v" if verbose else "-O3", "-I", INCLUDE, "-c", os.path.join(CSRC, "kernels.cu"),
                "-o", obj_dev]
-    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-             for c in (host_cmd, dev_cmd)]
+    refit_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "refit.cu"), "-o", obj_refit]
+    cmds = (host_cmd, dev_cmd, refit_cmd)
+    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
-    for p, c, o in zip(procs, (host_cmd, dev_cmd), outs):
+    for p, c, o in zip(procs, cmds, outs):
         if p.returncode != 0:
             raise RuntimeError(f"build failed: {' '.join(c)}\n{o}")
         if verbose and o:
             print(o)
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, obj_host, obj_dev]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, obj_host, obj_dev, obj_refit]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")

@@ -177,8 +177,9 @@ struct Builder {
   }
 
   // true when every |d.v| / 2^e < 2^30
+  int headroom = 0;  // lattice bits kept free for refits (CBVH_OPT_LATTICE_HEADROOM)
   bool fits(int ex) const {
-    const int64_t L = int64_t(1) << 30;
+    const int64_t L = int64_t(1) << (30 - headroom);
     for (int64_t v = 0; v < nv; ++v)
       for (int j = 0; j < K; ++j) {
         double t[3];
@@ -322,6 +323,7 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
       return cbvh::fail(CBVH_ERR_MESH, "mesh has no extent");
     }
     int ex = std::ilogb(M) - 29;  // 2^(ilogb M + 1) > M: fits unless rounding says otherwise
+    E.headroom = cbvh::lattice_headroom();
     while (!E.fits(ex)) ++ex;
     while (E.fits(ex - 1)) --ex;
     if (ex < -120 || ex > 96) {
@@ -617,9 +619,12 @@ namespace cbvh {
 namespace {
 thread_local std::string g_err;
 std::atomic<int> g_packing{CBVH_PACK_TOP_DOWN};
+std::atomic<int> g_headroom{0};
 }  // namespace
 void set_treelet_packing(int p) { g_packing.store(p); }
 int treelet_packing() { return g_packing.load(); }
+void set_lattice_headroom(int bits) { g_headroom.store(bits); }
+int lattice_headroom() { return g_headroom.load(); }
 int fail(int code, const std::string &msg) {
   g_err = msg;
   return code;

@@ -21,6 +21,10 @@ struct cbvh_bvh {
   // device copy (caller-owned memory)
   void *dev_blob = nullptr;
   int device = -1;
+  // refit plan (cbvh_refit_prepare): node ranges of each tree level and each treelet depth,
+  // and the workspace holding the plan's device arrays
+  std::vector<int64_t> refit_level_start, refit_td_start;
+  void *refit_ws = nullptr;
 };
 
 namespace cbvh {
@@ -30,4 +34,9 @@ void clear_error();
 // Treelet formation used by cbvh_build (CBVH_PACK_*), set by cbvh_set_option.
 void set_treelet_packing(int packing);
 int treelet_packing();
+// Lattice bits cbvh_build keeps free (CBVH_OPT_LATTICE_HEADROOM), set by cbvh_set_option.
+void set_lattice_headroom(int bits);
+int lattice_headroom();
+// Adds to the process-wide count of kernels launched (cbvh_kernel_launches).
+void count_launches(int n);
 }  // namespace cbvh

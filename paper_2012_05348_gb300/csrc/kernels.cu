@@ -2162,6 +2162,10 @@ extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t w
   return CBVH_OK;
 }
 
+namespace cbvh {
+void count_launches(int n) { g_launches.fetch_add(n); }
+}  // namespace cbvh
+
 extern "C" int cbvh_kernel_launches(int64_t *count) {
   cbvh::clear_error();
   if (!count) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
@@ -2184,6 +2188,11 @@ extern "C" int cbvh_set_option(int option, int64_t value) {
   if (option == CBVH_OPT_SPLIT) {
     if (value < 0 || value > 4) return cbvh::fail(CBVH_ERR_ARG, "split must be 0, 1, 2, 3 or 4");
     g_split.store((int)value);
+    return CBVH_OK;
+  }
+  if (option == CBVH_OPT_LATTICE_HEADROOM) {
+    if (value < 0 || value > 8) return cbvh::fail(CBVH_ERR_ARG, "lattice headroom must be in [0, 8] bits");
+    cbvh::set_lattice_headroom((int)value);
     return CBVH_OK;
   }
   if (option == CBVH_OPT_TREELET_PACKING) {

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "icosphere", "heightfield", "ValueNoise2D", "box_mesh", "capsule", "shoemake_rotations",
     "poses_box", "poses_terrain", "dh_link_poses", "merge_meshes", "transform_mesh",
-    "scene_diameter", "C1", "C2", "C3", "C4", "C5", "clutter", "arm_links",
+    "scene_diameter", "C1", "C2", "C3", "C4", "C5", "clutter", "arm_links", "self_pairs", "relative_poses",
 ]
 
 _PHI = (1.0 + math.sqrt(5.0)) / 2.0
@@ -453,3 +453,24 @@ def C4(rate: float, seconds: float, height_fn, seed: int = 2004, max_poses: int 
             P = poses_box(n, seed=sub, lo=-2.0, hi=2.0)
         reqs.append((env, robot, kind, P))
     return gaps, reqs
+
+
+def self_pairs(n_links: int = 6, gap: int = 2):
+    """Link pairs checked for self-collision: (i, j) with j >= i + gap (neighbours share a
+    joint and are allowed to touch)."""
+    return [(i, j) for i in range(n_links) for j in range(i + gap, n_links)]
+
+
+def relative_poses(link_poses: np.ndarray, i: int, j: int) -> np.ndarray:
+    """Pose of link j in link i's frame for every configuration: T_i^-1 T_j, in FP64 and
+    rounded to FP32.  link_poses: (n, L, 12) with x_world = R x_link + t."""
+    P = np.asarray(link_poses, dtype=np.float64)
+    Ri, ti = P[:, i, :9].reshape(-1, 3, 3), P[:, i, 9:]
+    Rj, tj = P[:, j, :9].reshape(-1, 3, 3), P[:, j, 9:]
+    RiT = np.transpose(Ri, (0, 2, 1))
+    R = RiT @ Rj
+    t = np.einsum("nab,nb->na", RiT, tj - ti)
+    out = np.empty((len(P), 12))
+    out[:, :9] = R.reshape(-1, 9)
+    out[:, 9:] = t
+    return out.astype(np.float32)

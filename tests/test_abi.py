@@ -140,3 +140,33 @@ def test_kernel_launch_counter_without_gpu(cb):
     n = cb.kernel_launches()
     assert n >= 0 and cb.kernel_launches() == n
     assert cb.lib.cbvh_kernel_launches(None) == -1
+
+
+def test_refit_host_checks(cb):
+    """Refit entry points without a device: the workspace size is host arithmetic; an
+    unattached handle is rejected before anything reaches the GPU."""
+    import ctypes as C
+    v, t = synth.icosphere(2, 1.0, 0.1, seed=1)
+    h = cb.BVH(v, t, 18, 4, 8, 4096, device=None)
+    nb = C.c_int64()
+    assert cb.lib.cbvh_refit_workspace_bytes(h.handle, C.byref(nb)) == 0
+    assert nb.value >= h.info["n_nodes"] * (24 + 16 * 9)
+    assert cb.lib.cbvh_refit(h.handle, C.c_void_p(16), 3, C.c_void_p(16), C.c_void_p(256), nb.value,
+                             C.c_void_p(16), None) == -9  # CBVH_ERR_STATE
+
+
+@pytest.mark.parametrize("headroom", [1, 3])
+def test_blob_identical_with_lattice_headroom(cb, headroom):
+    """CBVH_OPT_LATTICE_HEADROOM: the library and the oracle choose the same coarser lattice
+    (bounds below 2^(30 - headroom) steps) and write the same bytes."""
+    v, t = synth.icosphere(3, 1.0, 0.15, seed=8)
+    cb.set_option(cb.OPT_LATTICE_HEADROOM, headroom)
+    try:
+        h = cb.BVH(v, t, 24, 8, 8, 16384, device=None)
+    finally:
+        cb.set_option(cb.OPT_LATTICE_HEADROOM, 0)
+    o = oracle.BVH(v, t, 24, 8, 8, 16384, headroom=headroom)
+    o0 = oracle.BVH(v, t, 24, 8, 8, 16384)
+    assert o.e == o0.e + headroom and h.info["lattice_exp"] == o.e
+    assert (h.blob_host() == o.blob()).all()
+    assert cb.lib.cbvh_set_option(cb.OPT_LATTICE_HEADROOM, 9) == -1

@@ -132,3 +132,30 @@ def test_arm_sweep_against_oracle(cb, scene):
         assert (outs[i][:60][ok] == hit[ok]).all()
         checked += int(ok.sum())
     assert checked > 200
+
+
+def test_arm_self_collision_against_oracle(cb, scene):
+    """Self-collision of the arm: every non-adjacent link pair, link j posed in link i's
+    frame, all in one batch; flags match the oracle on configurations away from contact."""
+    c3 = scene["c3"]
+    pairs = synth.self_pairs(6)
+    n = 80
+    rel = {(i, j): synth.relative_poses(c3["link_poses"][:n], i, j) for i, j in pairs}
+    import torch
+    items = [dict(A=scene["links"][i], B=scene["links"][j], kind="collide",
+                  poses=torch.as_tensor(rel[i, j], device="cuda"), early_exit=True) for i, j in pairs]
+    outs = [o.cpu().numpy() for o in cb.Batch(items).run()]
+    checked = 0
+    for (i, j), got in zip(pairs, outs):
+        vi, ti = c3["links"][i]
+        vj, tj = c3["links"][j]
+        Ao = oracle.BVH(vi, ti, 24, 8, 8, 16384)
+        Bo = oracle.BVH(vj, tj, 24, 8, 8, 16384)
+        D = synth.scene_diameter(vi, vj)
+        near, _ = oracle.near_contact(Ao, Bo, rel[i, j], 1e-6 * D)
+        hit, *_ = oracle.collide(Ao, Bo, rel[i, j])
+        assert (got[~near] == hit[~near]).all(), (i, j)
+        checked += int((~near).sum())
+    assert checked > 600
+    hits = np.stack(outs).any(0)
+    assert 0 < hits.sum() < n  # some configurations fold onto themselves, some do not

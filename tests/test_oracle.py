@@ -464,3 +464,65 @@ def test_near_contact_filter_against_brute_force(c1_small):
         assert sorted(amb) == [tuple(x) for x in n_ij[n_off[p]:n_off[p + 1]].tolist()]
         if math.isfinite(mmin) and mmin <= eps:
             assert margin[p] == pytest.approx(mmin, rel=1e-12)
+
+
+
+@pytest.mark.parametrize("k,m,bits", [(18, 4, 8), (24, 8, 16), (18, 4, 1), (6, 2, 0)])
+def test_refit_bounds_exact_and_encoding_valid(k, m, bits):
+    """or_refit (deforming meshes): the tree and lattice exponent stay; every node's lattice
+    bounds are the exact floor/ceil (rationals) of the new vertices' projections; the new
+    blob decodes, with the independent decoder, to bounds that contain them; refitting back
+    to the original vertices restores the original blob byte for byte."""
+    v, t = _tiny_mesh(11 + k)
+    h = oracle.BVH(v, t, k, m, bits, 4096)
+    blob0, e0, tr0 = h.blob(), h.e, h.tree()
+    rng = np.random.default_rng(5)
+    v2 = (v * 1.1 + rng.uniform(-0.05, 0.05, size=v.shape)).astype(np.float32)
+    h.refit(v2)
+    assert h.e == e0
+    tr = h.tree()
+    assert all((tr[key] == tr0[key]).all() for key in tr)
+    K = k // 2
+    lat = h.lattice()
+    sets = [None] * h.n_nodes
+    for x in range(h.n_nodes - 1, -1, -1):
+        sets[x] = [int(tr["tri"][x])] if tr["nchild"][x] == 0 else \
+            sum((sets[tr["first"][x] + c] for c in range(tr["nchild"][x])), [])
+    scale = Fraction(2) ** h.e
+    for x in range(0, h.n_nodes, 3):
+        pts = [v2[i] for tri in sets[x] for i in t[tri]]
+        for j in range(K):
+            xs = [sum(Fraction(DIRS[j][c]) * Fraction(float(p[c])) for c in range(3)) / scale for p in pts]
+            assert lat["exact"][x, j, 0] == math.floor(min(xs)) and lat["exact"][x, j, 1] == math.ceil(max(xs))
+    _, f, _ = oracle.decode_blob(h.blob())
+    pl = h.placement()
+    order = np.lexsort((pl["local"], pl["treelet"]))
+    ex = lat["exact"][order].astype(np.float64)
+    assert (f[..., 0].astype(np.float64) <= np.ldexp(ex[..., 0], h.e)).all()
+    assert (f[..., 1].astype(np.float64) >= np.ldexp(ex[..., 1], h.e)).all()
+    h.refit(v)
+    assert (h.blob() == blob0).all()
+
+
+def test_lattice_headroom_exponent():
+    """With headroom h the exponent is the smallest with every |d.v| / 2^e < 2^(30 - h)."""
+    v, t = _tiny_mesh(4)
+    for h_bits in (0, 2, 5):
+        h = oracle.BVH(v, t, 18, 4, 8, 4096, headroom=h_bits)
+        vals = [sum(Fraction(d[c]) * Fraction(float(p[c])) for c in range(3)) for p in v for d in DIRS[:9]]
+        M = max(abs(x) for x in vals)
+        assert M / Fraction(2) ** h.e < 2 ** (30 - h_bits)
+        assert not (M / Fraction(2) ** (h.e - 1) < 2 ** (30 - h_bits))
+
+
+def test_refit_rejects_vertices_outside_the_lattice():
+    v, t = _tiny_mesh(2)
+    h = oracle.BVH(v, t, 18, 4, 8, 4096)
+    blob0 = h.blob()
+    with pytest.raises(oracle.OracleError):
+        h.refit(v * 4096.0)  # far beyond the 2^30 steps of the build's lattice
+    bad = v.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(oracle.OracleError):
+        h.refit(bad)
+    assert (h.blob() == blob0).all()
