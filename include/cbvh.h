@@ -237,13 +237,13 @@ int cbvh_set_option(int option, int64_t value);
  * build's tree with the new vertices (the host copy from cbvh_blob_host is not updated).
  * A deformation that reorders the median splits leaves the tree valid but less tight;
  * rebuild when it matters.
- *   cbvh_refit_workspace_bytes: device bytes of the plan and scratch (about 24 B per node
- *     + 16 B per node and direction).
+ *   cbvh_refit_workspace_bytes: device bytes of the plan and scratch (about 24 B per node,
+ *     16 B per node and direction, 8 B per vertex and direction).
  *   cbvh_refit_prepare: writes the node plan into `workspace` (256-byte aligned, caller-
  *     owned, kept unchanged between refits) and synchronises `stream`; once per handle and
  *     workspace.
- *   cbvh_refit: verts_dev n_verts x 3 FP32 and tris_dev n_tris x 3 int32 (the build's
- *     triangles), device pointers; asynchronous on `stream`, no synchronisation, so it can
+ *   cbvh_refit: verts_dev n_verts x 3 FP32 (n_verts: the build's vertex count) and tris_dev
+ *     n_tris x 3 int32 (the build's triangles), device pointers; asynchronous on `stream`, no synchronisation, so it can
  *     be captured in a CUDA graph.  A vertex that is not finite or leaves the lattice's
  *     range (|d.v| >= 2^30 steps), or a bound beyond +-65504 for quant_bits = 1, sets
  *     `status` to CBVH_ERR_MESH; the blob is then unspecified until a successful refit.

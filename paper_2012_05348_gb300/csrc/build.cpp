@@ -556,6 +556,7 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   }
   h->max_tdepth = max_td;
   h->n_tris = n_tris;
+  h->n_verts = n_verts;
   h->n_nodes = nn;
   h->n_treelets = ntl;
   // header

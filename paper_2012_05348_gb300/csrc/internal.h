@@ -15,7 +15,7 @@ struct cbvh_bvh {
   int max_tdepth = 0;  // deepest node below its treelet root
   int depth = 0;       // tree depth
   int rec_bytes = 0, root_bytes = 0;
-  int64_t n_tris = 0, n_nodes = 0, n_treelets = 0;
+  int64_t n_tris = 0, n_nodes = 0, n_treelets = 0, n_verts = 0;
   int64_t off_treelets = 0, off_tris = 0;
   std::vector<uint8_t> blob;  // host copy of the blob
   // device copy (caller-owned memory)

@@ -9,8 +9,10 @@
 // arrays in the caller's workspace: record offset, parent, leaf slot, depth in the tree and
 // below the treelet root, and two node orders (by tree depth for the bottom-up bounds, by
 // treelet depth for the top-down encoding).  Each refit is then a few kernels per level:
-//   1. leaves: exact floor / ceil of d_j . v / 2^e over their triangle's three vertices
-//      (Shewchuk's expansion arithmetic in FP64), the new triangle into the table;
+//   0. every vertex: exact floor / ceil of d_j . v / 2^e (Shewchuk's expansion arithmetic in
+//      FP64, after a fast path that decides most cases from the rounded sum);
+//   1. leaves: the interval over their triangle's three vertices, the new triangle into the
+//      table;
 //   2. every node, deepest level first: its bounds merged into its parent's by atomicMin /
 //      atomicMax (a parent's level runs after all of its children's);
 //   3. treelet depth 0, 1, ...: decoded interval from the parent's (correctors rounded
@@ -47,6 +49,12 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
 // the smaller components cannot move the sum across an integer, so the floor is q2's; if q2
 // is an integer the same holds one component down.
 __device__ long long floor3_exact(double a, double b, double c) {
+  // fast path: the rounded sum is off by at most 2u (|a| + |b| + |c|) (two additions, u =
+  // 2^-53); when twice that margin cannot reach an integer, its floor is the exact floor
+  const double sum = __dadd_rn(__dadd_rn(a, b), c);
+  const double slack = (fabs(a) + fabs(b) + fabs(c)) * 0x1p-51;
+  const double fl = floor(__dsub_rn(sum, slack));
+  if (fl == floor(__dadd_rn(sum, slack))) return (long long)fl;
   double x1, y1;
   two_sum(a, b, x1, y1);  // expansion [y1, x1]
   double q, q0, q1, q2;
@@ -102,6 +110,7 @@ __device__ __forceinline__ float f32_up(int L, float scale) { return __int2float
 __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
 
 struct RefitArgs {
+  int32_t *VL;  // [n_verts][K][2] lattice interval of every vertex
   uint8_t *blob;
   int64_t off_tris;
   const float *verts;
@@ -120,6 +129,31 @@ struct RefitArgs {
   int32_t *D;  // [nn][K][2] decoded bounds
   int32_t *status;
 };
+
+// One thread per (vertex, direction): the vertex's lattice interval.  A vertex that is not
+// finite fails the refit (the builder rejects such meshes); the range rule is applied by the
+// leaves, to the vertices triangles use.
+__global__ void vertex_lattice(const RefitArgs a) {
+  const int64_t items = a.n_verts * a.K;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = it / a.K;
+    const int j = (int)(it - v * a.K);
+    const float p[3] = {a.verts[3 * v], a.verts[3 * v + 1], a.verts[3 * v + 2]};
+    int32_t *out = a.VL + 2 * it;
+    if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) {
+      set_status(a.status, CBVH_ERR_MESH);
+      out[0] = INT32_MAX;
+      out[1] = INT32_MIN;
+      continue;
+    }
+    long long lo, hi;
+    lattice_of(p, j, a.inv, lo, hi);
+    // clamp to the int32 range; anything beyond the lattice's 2^30 fails at the leaf
+    out[0] = (int32_t)max(min(lo, (long long)INT32_MAX), (long long)INT32_MIN);
+    out[1] = (int32_t)max(min(hi, (long long)INT32_MAX), (long long)INT32_MIN);
+  }
+}
 
 __global__ void init_bounds(int32_t *C, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -148,21 +182,16 @@ __global__ void bounds_level(const RefitArgs a) {
           bad = true;
           break;
         }
-        const float v[3] = {a.verts[3 * (int64_t)vi], a.verts[3 * (int64_t)vi + 1], a.verts[3 * (int64_t)vi + 2]};
-        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
-          bad = true;
-          break;
-        }
-        long long l, h;
-        lattice_of(v, j, a.inv, l, h);
+        const int32_t *L = a.VL + ((int64_t)vi * a.K + j) * 2;
+        const long long l = L[0], h = L[1];
         if (l > kLatLimit - 1 || h < -(kLatLimit - 1)) bad = true;  // the builder's range rule
         lo = min(lo, l);
         hi = max(hi, h);
         if (j == 0) {
           float *dst = reinterpret_cast<float *>(T + 16 * c);
-          dst[0] = v[0];
-          dst[1] = v[1];
-          dst[2] = v[2];
+          dst[0] = a.verts[3 * (int64_t)vi];
+          dst[1] = a.verts[3 * (int64_t)vi + 1];
+          dst[2] = a.verts[3 * (int64_t)vi + 2];
         }
       }
       if (bad) {
@@ -241,7 +270,7 @@ int64_t al256(int64_t x) { return (x + 255) & ~int64_t(255); }
 
 // Byte offsets of the plan's arrays in the workspace.
 struct RefitLayout {
-  int64_t rec_off, parent, leaf, tdepth, by_level, by_td, C, D, total;
+  int64_t rec_off, parent, leaf, tdepth, by_level, by_td, C, D, VL, total;
 };
 RefitLayout refit_layout(const cbvh_bvh *h) {
   const int64_t nn = h->n_nodes;
@@ -263,6 +292,8 @@ RefitLayout refit_layout(const cbvh_bvh *h) {
   o = al256(o + 8 * nn * h->K);
   L.D = o;
   o = al256(o + 8 * nn * h->K);
+  L.VL = o;
+  o = al256(o + 8 * h->n_verts * h->K);
   L.total = o;
   return L;
 }
@@ -377,7 +408,7 @@ extern "C" int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, 
   if (h->refit_ws != workspace) return cbvh::fail(CBVH_ERR_STATE, "workspace not prepared; call cbvh_refit_prepare");
   const RefitLayout L = refit_layout(h);
   if (workspace_bytes < L.total) return cbvh::fail(CBVH_ERR_WORKSPACE, "refit workspace too small");
-  if (n_verts < 3) return cbvh::fail(CBVH_ERR_ARG, "n_verts must be at least 3");
+  if (n_verts != h->n_verts) return cbvh::fail(CBVH_ERR_ARG, "a refit needs the build's vertex count");
   uint8_t *ws = static_cast<uint8_t *>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
@@ -402,10 +433,13 @@ extern "C" int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, 
   a.C = reinterpret_cast<int32_t *>(ws + L.C);
   a.D = reinterpret_cast<int32_t *>(ws + L.D);
   a.status = status;
+  a.VL = reinterpret_cast<int32_t *>(ws + L.VL);
   const int64_t nC = 2 * h->n_nodes * h->K;
   init_bounds<<<(unsigned)std::min<int64_t>((nC + 255) / 256, 4096), 256, 0, s>>>(a.C, nC);
   int launches = 1;
   auto grid = [](int64_t items) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 65535)); };
+  vertex_lattice<<<grid(n_verts * h->K), 256, 0, s>>>(a);
+  ++launches;
   a.order = reinterpret_cast<const int32_t *>(ws + L.by_level);
   const auto &ls = h->refit_level_start;
   for (int64_t d = (int64_t)ls.size() - 2; d >= 0; --d) {  // deepest level first
