@@ -220,13 +220,28 @@ __device__ __forceinline__ const uint8_t *tbase(const BVd &X, const Side &S, uin
 // refreshing the cache on the way.  Returns x's record; all lanes must call it.
 // w0: the first word of x's record (the caller has it); S.cur_t / cur_base must hold x's
 // treelet.
-__device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, int lane, int2 &P) {
+__device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, const uint8_t *rx, int lane,
+                             int2 &P) {
   const uint32_t t = x >> X.lbits, l = x & X.lmask;
   uint32_t w = w0;
   const int d = (int)(w >> 24);
+  const uint32_t tb = t << X.lbits;
+  const bool act = lane < S.nd;
+  // fast paths of depth-first order: x itself cached, or its parent cached (one corrector)
+  if (S.tag[d] == (tb | l)) {
+    if (act) P = S.lat[d * S.nd + lane];
+    return;
+  }
+  if (d > 0 && S.tag[d - 1] == (tb | (w & 0xffffu))) {
+    if (act) {
+      P = apply_delta(S.lat[(d - 1) * S.nd + lane], rx, X.bits, lane);
+      S.lat[d * S.nd + lane] = P;
+    }
+    if (lane == 0) S.tag[d] = tb | l;
+    return;  // the caller synchronises the warp before anyone reads the cache
+  }
   int dd = d, start = -1;
   uint32_t ll = l;
-  const uint32_t tb = t << X.lbits;
   for (;;) {
     if (S.tag[dd] == (tb | ll)) {
       start = dd;
@@ -243,7 +258,6 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, int
     w = ld32(rec_at(X, S.cur_base, ll));  // not cached: its record leads one level up
   }
   __syncwarp();
-  const bool act = lane < S.nd;
   if (start < 0) {
     if (act) {
       P = abs_lattice(rec_at(X, S.cur_base, 0), lane);
@@ -322,9 +336,9 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     __syncwarp();
     return self ? 1 : nc;
   }
+  int2 P = make_int2(0, 0);  // x's decoded interval (lanes < nd)
   if (self || !ext) {
-    int2 P;
-    chain_decode(X, S, x, w0, lane, P);
+    chain_decode(X, S, x, w0, rx, lane, P);
     if (self) {
       if (lane < nd) iv[lane] = lat_to_f(P, X.scale);
       if (lane == 0) {
@@ -336,10 +350,8 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     }
   }
   const int d = (int)(w0 >> 24);
-  if (!ext) {  // the children's corrector shifts, one per direction
-    if (lane < nd) shift[lane] = delta_shift(S.lat[d * nd + lane], X.bits);
-    __syncwarp();
-  }
+  if (!ext && lane < nd) shift[lane] = delta_shift(P, X.bits);  // the children's corrector shifts
+  __syncwarp();
   for (int it = lane; it < nc * nd; it += 32) {
     const int i = it / nd, j = it - i * nd;
     const uint8_t *rc;
