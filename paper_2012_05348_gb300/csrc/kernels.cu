@@ -993,7 +993,10 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       // test every member pair; survivors are compacted by ballot onto the stack (inner
       // pairs) or the leaf queue (leaf pairs)
       const int np = na * nb;
-      const unsigned inv_nb = c_inv16[nb];  // it / nb == (it * inv_nb) >> 16 for it < 256
+      // pairs in B-major order: the pair popped next shares B's projected set with the one
+      // before (a B change costs a decode and a projection on all of A's directions, about
+      // twice an A decode)
+      const unsigned inv_na = c_inv16[na];  // it / na == (it * inv_na) >> 16 for it < 256
       n_bv += np;
       float run_lb = INFINITY;  // PQ: smallest lower bound pushed by this expansion ...
       int run_pos = -1;         // ... and its stack slot
@@ -1003,8 +1006,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         int i = 0, j = 0;
         float lb = INFINITY;
         if (it < np) {
-          i = (int)(((unsigned)it * inv_nb) >> 16);
-          j = it - i * nb;
+          j = (int)(((unsigned)it * inv_na) >> 16);
+          i = it - j * na;
           const float2 *av = aiv + i * KS, *pv = piv + j * KS;
           if (MODE == MODE_CD) {
             keep = true;
