@@ -1090,7 +1090,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       }
       if (done || sp == 0) break;
       // ---------------- donate the bottom of the stack to waiting warps ----------------
-      if (p.queue && sp >= 2 && expansions >= p.budget && (expansions & 31) == 0) {
+      // (checked every 64 expansions: the check reads two global counters)
+      if (p.queue && sp >= 2 && expansions >= p.budget && (expansions & 63) == 0) {
         int want = 0;
         if (lane == 0) {
           const int waiting = (int)(*reinterpret_cast<volatile unsigned int *>(&qc[1]) -
