@@ -111,7 +111,9 @@ int cbvh_workspace_bytes(const cbvh_bvh *A, const cbvh_bvh *B, int64_t n_poses, 
                          int64_t *bytes);
 
 /* Collision detection, Algorithm 1 with checkPrimitives = closed triangle-triangle
- * intersection, for n poses of B against A.
+ * intersection, for n poses of B against A.  "a and b intersect" is tested both ways,
+ * rounded outward: B's box moved by the pose against A's k-DOP slabs, then A's axis box
+ * moved into B's frame against B's box (a leaf of B: its triangle's box).
  *   poses: n x 12 FP32.  hit: n bytes, 1 if any triangle of A meets a triangle of R B + t.
  *   pair_offsets (n + 1 int64) and pairs (2 x pair_capacity int32, (i, j) = (triangle of A,
  *   triangle of B)): the per-pose intersecting pairs in CSR form, or both NULL.

@@ -80,7 +80,7 @@ struct Layout {
   int o_pose;
   int o_tagA, o_latA, o_pathA;
   int o_tagB, o_latB, o_pathB;
-  int o_aset, o_bset, o_bvd, o_shift;
+  int o_aset, o_bset, o_bvd, o_shift, o_abox;
   int KS;  // row stride (floats) of the per-child direction arrays
 };
 
@@ -736,6 +736,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
   uint32_t *bref = reinterpret_cast<uint32_t *>(piv + kMaxM * KS);
   uint32_t *bleaf = bref + kMaxM;
   int *shift = reinterpret_cast<int *>(ws + p.L.o_shift);
+  float2 *abox = reinterpret_cast<float2 *>(ws + p.L.o_abox);  // [i][3], valid while abox_ok
+  bool abox_ok = false;
   for (int i = lane; i <= p.L.tdA; i += 32) SA.tag[i] = 0xffffffffu;
   for (int i = lane; i <= p.L.tdB; i += 32) SB.tag[i] = 0xffffffffu;
   __syncwarp();
@@ -857,6 +859,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
     const uint32_t pose = (uint32_t)(gid - item_lo);  // pose index within its query
     if ((int64_t)gid != cur_pose) {
       keyB = 0xffffffffu;  // projections depend on the pose
+      abox_ok = false;
       // ---- pose precompute: u_j = R^T d_j, |u_j|, [s_lo, s_hi] of d_j.t, and eta_j, a
       // bound on the rounding error of each component of u_j ----
       cur_pose = gid;
@@ -970,12 +973,21 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         na = decode_set<KA>(A, SA, a, root, lane, aiv, KS, aref, aleaf, shift);
         keyA = root ? 0xffffffffu : a;
         na_c = na;
+        abox_ok = false;
       } else {
         na = na_c;
       }
       if (b != keyB || root) {
         nb = decode_set<3>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
         if (lane < nb && bleaf[lane] == 0xffffffffu) member_box(bvv, lane, bcm[lane], bhm[lane]);
+        if (MODE == MODE_CD && lane < 3 * nb) {  // leaf members: the exact box of their triangle
+          const int i = lane / 3, x = lane - 3 * i;
+          if (bleaf[i] != 0xffffffffu) {
+            const float *T = reinterpret_cast<const float *>(B.tris + 3 * (size_t)bleaf[i]);
+            const float v0 = T[x], v1 = T[4 + x], v2 = T[8 + x];
+            bvv[i * 4 + x] = make_float2(fminf(v0, fminf(v1, v2)), fmaxf(v0, fmaxf(v1, v2)));
+          }
+        }
         __syncwarp();
         for (int it = lane; it < nb * KA; it += 32) {
           const int i = it / KA, j = it - i * KA;
@@ -992,6 +1004,29 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       ++n_exp;
       // test every member pair; survivors are compacted by ballot onto the stack (inner
       // pairs) or the leaf queue (leaf pairs)
+      if (MODE == MODE_CD && !abox_ok) {
+        // A's members' axis boxes in B's frame: along B's axis k (world direction u = column k
+        // of R, exact) the box projects to u.c - u.t +- |u|.h, all rounded outward
+        for (int it = lane; it < 3 * na; it += 32) {
+          const int i = it / 3, k = it - 3 * i;
+          float c[3], h[3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const float2 v = aiv[i * KS + x];
+            c[x] = __fmul_rn(__fadd_rn(v.x, v.y), 0.5f);
+            h[x] = fmaxf(__fsub_ru(v.y, c[x]), __fsub_ru(c[x], v.x));
+          }
+          const float u0 = pc[k], u1 = pc[3 + k], u2 = pc[6 + k];
+          const float uc_lo = __fmaf_rd(u0, c[0], __fmaf_rd(u1, c[1], __fmul_rd(u2, c[2])));
+          const float uc_hi = __fmaf_ru(u0, c[0], __fmaf_ru(u1, c[1], __fmul_ru(u2, c[2])));
+          const float ut_lo = __fmaf_rd(u0, pc[9], __fmaf_rd(u1, pc[10], __fmul_rd(u2, pc[11])));
+          const float ut_hi = __fmaf_ru(u0, pc[9], __fmaf_ru(u1, pc[10], __fmul_ru(u2, pc[11])));
+          const float r = __fmaf_ru(fabsf(u0), h[0], __fmaf_ru(fabsf(u1), h[1], __fmul_ru(fabsf(u2), h[2])));
+          abox[i * 3 + k] = make_float2(__fsub_rd(__fsub_rd(uc_lo, ut_hi), r), __fadd_ru(__fsub_ru(uc_hi, ut_lo), r));
+        }
+        __syncwarp();
+        abox_ok = true;
+      }
       const int np = na * nb;
       // pairs in B-major order: the pair popped next shares B's projected set with the one
       // before (a B change costs a decode and a projection on all of A's directions, about
@@ -1015,6 +1050,11 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
             for (int d = 0; d < KA; ++d) {
               const float2 x = av[d], y = pv[d];
               keep &= (x.x <= y.y) & (y.x <= x.y);
+            }
+            if (keep) {  // and B's own axes: A's box moved into B's frame against B's box
+              const float2 *ab = abox + i * 3, *bb = bvv + j * 4;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) keep &= (ab[k].x <= bb[k].y) & (bb[k].x <= ab[k].y);
             }
           } else {
             // two lower bounds, all rounded down: the widest slab gap over |d|, and the
@@ -1440,6 +1480,8 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   o = align16(o + 2 * (int)sizeof(BVd));
   L.o_shift = o;  // corrector shifts of the set being decoded, one per direction
   o = align16(o + 4 * kMaxK);
+  L.o_abox = o;  // A members' axis boxes moved into B's frame (CD), (lo, hi) per B axis
+  o = align16(o + 8 * 3 * kMaxM);
   L.warp_bytes = o;
   return L;
 }
