@@ -127,9 +127,10 @@ int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64
 
 /* Proximity query: dist[p] = minimum distance between the triangles of A and those of
  * R_p B + t_p (0 when they intersect), by branch-and-bound Algorithm 1.  A node pair is
- * pruned when its lower bound reaches the best distance found: the larger of the widest
- * slab gap over |d_j| and the distance between the two axis boxes (root of the summed
- * squared x, y and z gaps), both rounded down.  A collision pass with early exit runs
+ * pruned when its lower bound reaches the best distance found: the largest of the widest
+ * slab gap over |d_j|, the distance between the two axis boxes (root of the summed squared
+ * x, y and z gaps), and the same distance in B's frame (A's box moved into it), all
+ * rounded down.  A collision pass with early exit runs
  * first and settles the intersecting poses at 0.  FP32; accurate to a few ulps of the
  * scene size. */
 int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist, void *workspace,

@@ -980,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       if (b != keyB || root) {
         nb = decode_set<3>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
         if (lane < nb && bleaf[lane] == 0xffffffffu) member_box(bvv, lane, bcm[lane], bhm[lane]);
-        if (MODE == MODE_CD && lane < 3 * nb) {  // leaf members: the exact box of their triangle
+        if (lane < 3 * nb) {  // leaf members: the exact box of their triangle
           const int i = lane / 3, x = lane - 3 * i;
           if (bleaf[i] != 0xffffffffu) {
             const float *T = reinterpret_cast<const float *>(B.tris + 3 * (size_t)bleaf[i]);
@@ -1004,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       ++n_exp;
       // test every member pair; survivors are compacted by ballot onto the stack (inner
       // pairs) or the leaf queue (leaf pairs)
-      if (MODE == MODE_CD && !abox_ok) {
+      if (!abox_ok) {
         // A's members' axis boxes in B's frame: along B's axis k (world direction u = column k
         // of R, exact) the box projects to u.c - u.t +- |u|.h, all rounded outward
         for (int it = lane; it < 3 * na; it += 32) {
@@ -1057,8 +1057,9 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
               for (int k = 0; k < 3; ++k) keep &= (ab[k].x <= bb[k].y) & (bb[k].x <= ab[k].y);
             }
           } else {
-            // two lower bounds, all rounded down: the widest slab gap over |d|, and the
-            // distance between the axis boxes, sqrt of the squared gaps along x, y and z
+            // three lower bounds, all rounded down: the widest slab gap over |d|, the
+            // distance between the axis boxes (root of the squared x, y and z gaps), and the
+            // same in B's frame
             lb = 0.f;
             float box2 = 0.f;
 #pragma unroll
@@ -1071,7 +1072,14 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
                 box2 = __fmaf_rd(gp, gp, box2);
               }
             }
-            lb = fmaxf(lb, __fsqrt_rd(box2));
+            const float2 *ab = abox + i * 3, *bb = bvv + j * 4;  // A's box moved into B's frame
+            float box2b = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const float g = fmaxf(fmaxf(__fsub_rd(ab[k].x, bb[k].y), __fsub_rd(bb[k].x, ab[k].y)), 0.f);
+              box2b = __fmaf_rd(g, g, box2b);
+            }
+            lb = fmaxf(lb, __fsqrt_rd(fmaxf(box2, box2b)));
             keep = lb < best;
           }
         }
@@ -1480,7 +1488,7 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   o = align16(o + 2 * (int)sizeof(BVd));
   L.o_shift = o;  // corrector shifts of the set being decoded, one per direction
   o = align16(o + 4 * kMaxK);
-  L.o_abox = o;  // A members' axis boxes moved into B's frame (CD), (lo, hi) per B axis
+  L.o_abox = o;  // A members' axis boxes moved into B's frame, (lo, hi) per B axis
   o = align16(o + 8 * 3 * kMaxM);
   L.warp_bytes = o;
   return L;
