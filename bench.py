@@ -417,20 +417,45 @@ def compression(cb, torch, dev, c, steps=3):
 
 
 def refit_rate(cb, torch, dev, verts, tris, k, m, bits, tb, packing, reps=5):
-    """Device refit (deforming meshes) of one hierarchy: the mesh breathes (every vertex
-    scaled about the origin by 1 +- 0.1 %), the tree is kept and every bound recomputed and
-    re-encoded on the GPU.  Algorithmic bytes: per triangle its index, three vertex indices,
-    three vertices in and the triangle out (88 B); per node the plan (24 B), the exact
-    bounds written, merged and read back and the decoded bounds (24 B per direction) and its
-    record."""
+    """Device refit (deforming meshes) and device build (per-frame meshes) of one hierarchy.
+
+    Refit: the mesh breathes (every vertex scaled about the origin by 1 +- 0.1 %), the tree
+    is kept and every bound recomputed and re-encoded on the GPU.  Algorithmic bytes: per
+    triangle its index, three vertex indices, three vertices in and the triangle out
+    (88 B); per node the plan (24 B), the exact bounds written, merged and read back and
+    the decoded bounds (24 B per direction) and its record.
+
+    Build: the host builder (one core) against cbvh_build_device on a plan made once (the
+    median splits, lattice exponent, bounds and encoding on the GPU; the call synchronises),
+    without and with the copy of the blob back to the host; the device blob must equal the
+    host build's byte for byte."""
     cb.set_option(cb.OPT_TREELET_PACKING, packing)
     cb.set_option(cb.OPT_LATTICE_HEADROOM, 1)  # room for the larger breath
     try:
+        t0 = time.perf_counter()
         h = cb.BVH(verts, tris, k, m, bits, tb, device=dev)
+        host_build_s = time.perf_counter() - t0
+        p = cb.BVH.plan(len(verts), len(tris), k, m, bits, tb, device=dev)
     finally:
         cb.set_option(cb.OPT_TREELET_PACKING, cb.PACK_TOP_DOWN)
         cb.set_option(cb.OPT_LATTICE_HEADROOM, 0)
     T = torch.as_tensor(tris, device=dev)
+    V0 = torch.as_tensor(verts, device=dev)
+    p.build_device(V0, T, host_copy=False)  # first build: workspace and plan upload
+    build_ms = []
+    n0 = cb.kernel_launches()
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p.build_device(V0, T, host_copy=False)
+        build_ms.append((time.perf_counter() - t0) * 1e3)
+    launches = (cb.kernel_launches() - n0) // reps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p.build_device(V0, T, host_copy=True)
+    copy_ms = (time.perf_counter() - t0) * 1e3
+    identical = bool((p.blob_host() == h.blob_host()).all())
+    del p
     V = [torch.as_tensor((verts * s).astype(np.float32), device=dev) for s in (1.001, 0.999)]
     h.refit(V[0], T)
     torch.cuda.synchronize()
@@ -444,8 +469,12 @@ def refit_rate(cb, torch, dev, verts, tris, k, m, bits, tb, packing, reps=5):
     nn, nt = h.info["n_nodes"], h.info["n_tris"]
     rec = 8 + (4 * k // 2 if bits == 1 else (8 * k // 2 if bits == 0 else k * bits // 8))
     algo = nt * 88 + nn * (24 + 24 * (k // 2) + rec)
+    bms = float(np.median(build_ms))
     return {"triangles": nt, "nodes": nn, "quant_bits": bits, "ms": ms, "triangles_per_s": nt / (ms / 1e3),
-            "algorithmic_gbs": algo / (ms * 1e6)}
+            "algorithmic_gbs": algo / (ms * 1e6),
+            "build": {"host_build_s": host_build_s, "device_build_ms": bms,
+                      "device_build_with_host_copy_ms": copy_ms, "speedup_vs_host": host_build_s * 1e3 / bms,
+                      "kernel_launches": launches, "identical_to_host_build": identical}}
 
 
 def _bv_bytes(k: int, bits: int) -> int:

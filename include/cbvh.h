@@ -257,6 +257,40 @@ int cbvh_refit_prepare(cbvh_bvh *h, void *workspace, int64_t workspace_bytes, vo
 int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, const int32_t *tris_dev, void *workspace,
                int64_t workspace_bytes, int32_t *status, void *stream);
 
+/* ---- device-side build for per-frame meshes ----
+ * The same hierarchy as cbvh_build, built on the GPU from a device mesh; the blob is
+ * byte-identical to cbvh_build's for the same mesh, parameters and options.  The shape of the
+ * tree (child counts, treelets, topology words) follows from the triangle count and the
+ * branching alone, since every node's triangles are halved log2(branching) times by the
+ * median split (Sec. III); the geometry only decides which triangle ends in which leaf, the
+ * lattice exponent and the bounds.
+ *   cbvh_build_plan: host, no mesh data.  A handle for meshes of n_verts vertices and
+ *     n_tris triangles: its blob holds the shape with zero bounds and an empty triangle table
+ *     (queries refuse it with CBVH_ERR_STATE until a device build succeeds).  Treelet packing
+ *     and lattice headroom are the options in force now.  Attach it (cbvh_attach) before
+ *     the first device build.  Errors as cbvh_build's parameter checks.
+ *   cbvh_build_device_workspace_bytes: device bytes of the build's scratch (about 110 B per
+ *     triangle, plus the refit plan of cbvh_refit_workspace_bytes at its front).
+ *   cbvh_build_device: verts_dev n_verts x 3 FP32, tris_dev n_tris x 3 int32 (device
+ *     pointers, the plan's counts); workspace 256-byte aligned, caller-owned.  Builds into
+ *     the attached blob on `stream` and synchronises it (the lattice exponent is read back
+ *     once).  May be called again with new geometry of the same counts (a new frame); the
+ *     workspace also serves cbvh_refit afterwards.  flags: CBVH_BUILD_HOST_COPY copies the
+ *     blob back into the host copy (cbvh_blob_host); without it the host copy is stale and
+ *     cbvh_blob_host / cbvh_attach refuse with CBVH_ERR_STATE.
+ *   The mesh checks are cbvh_build's, reported as CBVH_ERR_MESH: an out-of-range index, a
+ *   zero-area triangle, a non-finite vertex, no extent, coordinates outside the lattice's
+ *   range, bounds beyond +-65504 for quant_bits = 1.  On any error the handle has no
+ *   geometry until the next successful build.
+ * Errors: CBVH_ERR_ARG, CBVH_ERR_STATE (not a plan, not attached), CBVH_ERR_WORKSPACE,
+ * CBVH_ERR_MESH, CBVH_ERR_CUDA. */
+#define CBVH_BUILD_HOST_COPY 1u
+int cbvh_build_plan(int64_t n_verts, int64_t n_tris, int k, int branching, int quant_bits, int treelet_bytes,
+                    cbvh_bvh **out);
+int cbvh_build_device_workspace_bytes(const cbvh_bvh *h, int64_t *bytes);
+int cbvh_build_device(cbvh_bvh *h, const float *verts_dev, const int32_t *tris_dev, void *workspace,
+                      int64_t workspace_bytes, uint32_t flags, void *stream);
+
 /* Kernels this library has launched in this process so far (every traversal round, every
  * compaction kernel, the decode hook); a count the caller can difference around a region.
  * Host only; no synchronisation.  Errors: CBVH_ERR_ARG (NULL). */

@@ -64,11 +64,15 @@ def _declare(L):
     L.cbvh_refit_workspace_bytes.argtypes = [P, C.POINTER(I64)]
     L.cbvh_refit_prepare.argtypes = [P, P, I64, P]
     L.cbvh_refit.argtypes = [P, P, I64, P, P, I64, P, P]
+    L.cbvh_build_plan.argtypes = [I64, I64, I32, I32, I32, I32, C.POINTER(P)]
+    L.cbvh_build_device_workspace_bytes.argtypes = [P, C.POINTER(I64)]
+    L.cbvh_build_device.argtypes = [P, P, P, P, I64, U32, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
               "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
               "cbvh_profile_collect", "cbvh_distance_noalloc", "cbvh_batch_create", "cbvh_batch_free",
               "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option",
-              "cbvh_kernel_launches", "cbvh_refit_workspace_bytes", "cbvh_refit_prepare", "cbvh_refit"):
+              "cbvh_kernel_launches", "cbvh_refit_workspace_bytes", "cbvh_refit_prepare", "cbvh_refit",
+              "cbvh_build_plan", "cbvh_build_device_workspace_bytes", "cbvh_build_device"):
         getattr(L, f).restype = I32
     return L
 
@@ -131,12 +135,66 @@ class BVH:
         _check(_load().cbvh_build(v.ctypes.data_as(C.c_void_p), len(v), t.ctypes.data_as(C.c_void_p), len(t), k,
                               branching, quant_bits, treelet_bytes, C.byref(h)))
         self._h = h
-        info = _Info()
-        _check(_load().cbvh_info(h, C.byref(info)))
-        self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
+        self.n_verts = len(v)
+        self._refresh_info()
         self.blob_dev = None
         if device is not None:
             self.attach(device)
+
+    def _refresh_info(self):
+        info = _Info()
+        _check(_load().cbvh_info(self._h, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
+
+    @classmethod
+    def plan(cls, n_verts: int, n_tris: int, k: int = 18, branching: int = 4, quant_bits: int = 16,
+             treelet_bytes: int = 4096, device="cuda"):
+        """cbvh_build_plan: the hierarchy's shape for meshes of n_verts vertices and n_tris
+        triangles (host, no mesh data), attached to a device buffer; fill it with
+        build_device.  Queries refuse it until a device build succeeds."""
+        self = cls.__new__(cls)
+        h = C.c_void_p()
+        _check(_load().cbvh_build_plan(int(n_verts), int(n_tris), k, branching, quant_bits, treelet_bytes,
+                                       C.byref(h)))
+        self._h = h
+        self.n_verts = int(n_verts)
+        self._refresh_info()
+        self.blob_dev = None
+        if device is not None:
+            self.attach(device)
+        return self
+
+    @classmethod
+    def on_device(cls, verts, tris, k: int = 18, branching: int = 4, quant_bits: int = 16,
+                  treelet_bytes: int = 4096, host_copy: bool = True, stream=None):
+        """A hierarchy built on the GPU (cbvh_build_plan + cbvh_build_device) from device
+        tensors verts float32 (n_verts, 3) and tris int32 (n_tris, 3)."""
+        b = cls.plan(int(verts.shape[0]), int(tris.shape[0]), k, branching, quant_bits, treelet_bytes,
+                     device=verts.device)
+        return b.build_device(verts, tris, host_copy=host_copy, stream=stream)
+
+    def build_device(self, verts, tris, host_copy: bool = True, stream=None):
+        """cbvh_build_device: (re)build this plan's hierarchy on the GPU from device tensors
+        verts float32 (n_verts, 3) and tris int32 (n_tris, 3) of the plan's counts.  The
+        blob is byte-identical to the host build's; host_copy also refreshes blob_host()."""
+        torch = _torch()
+        if self.blob_dev is None:
+            raise CbvhError(-9, "not attached")
+        for name, t, dt, n in (("verts", verts, torch.float32, self.n_verts), ("tris", tris, torch.int32,
+                                                                              self.info["n_tris"])):
+            if (t.dtype != dt or t.device != self.blob_dev.device or not t.is_contiguous() or t.dim() != 2
+                    or t.shape[1] != 3 or t.shape[0] != n):
+                raise ValueError(f"{name}: need a contiguous {dt} tensor of shape ({n}, 3) on {self.blob_dev.device}")
+        if getattr(self, "_build_ws", None) is None:
+            nb = C.c_int64()
+            _check(_load().cbvh_build_device_workspace_bytes(self._h, C.byref(nb)))
+            self._build_ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=self.blob_dev.device)
+        with torch.cuda.device(self.blob_dev.device):
+            _check(_load().cbvh_build_device(self._h, _ptr(verts), _ptr(tris), _ptr(self._build_ws),
+                                             self._build_ws.numel(), 1 if host_copy else 0, _stream_ptr(stream)))
+        self._refit_ws = self._build_ws  # the build prepared the refit plan at the workspace's front
+        self._refresh_info()
+        return self
 
     @property
     def handle(self):

@@ -131,7 +131,9 @@ struct Builder {
     });
   }
 
-  void build_tree() {
+  // shape_only: no splits; every leaf records its position in the (device-sorted) order
+  // instead of a triangle, since the shape depends on the triangle count alone.
+  void build_tree(bool shape_only = false) {
     perm.resize(nt);
     std::iota(perm.begin(), perm.end(), 0);
     struct Item {
@@ -157,7 +159,7 @@ struct Builder {
             next.push_back({s, 1});
             continue;
           }
-          split(s, n);
+          if (!shape_only) split(s, n);
           next.push_back({s, n / 2});
           next.push_back({s + n / 2, n - n / 2});
         }
@@ -229,14 +231,227 @@ uint16_t half_up(double v) {
   return v > 0 ? half_pos(v, true) : (uint16_t)(0x8000u | half_pos(-v, false));
 }
 
-}  // namespace
+// Treelets, predictor-corrector encoding and serialisation of a built tree.  `nodes` in
+// BFS order (a leaf's `tri` is its triangle, or its position in the split order for a
+// plan), `lat` the exact lattice bounds of every node (zeros for a plan).  With verts_host
+// NULL the triangle table stays zero and the leaves' positions go to h->leaf_pos.
+int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_t> &lat, const float *verts_host,
+           const int32_t *tris_host, int64_t n_tris) {
+  const int k = h->k, K = h->K, branching = h->m, quant_bits = h->bits, treelet_bytes = h->treelet_bytes;
+  const int64_t nn = (int64_t)nodes.size();
+  for (const Node &nd : nodes) h->depth = std::max(h->depth, nd.depth);
+  // ---- treelets ----
+  std::vector<int32_t> tlet(nn), local(nn), child_tlet(nn, -1);
+  std::vector<uint8_t> ext(nn, 0);
+  std::vector<int32_t> roots{0};
+  std::vector<std::vector<int32_t>> members;
+  const int packing = cbvh::treelet_packing();
+  if (packing == CBVH_PACK_BOTTOM_UP) {
+    // Bottom-up: `carry` counts the nodes of a subtree not yet cut off.  A node keeps its
+    // children while it and everything they carry fit one treelet; else every child roots
+    // a treelet of its own.  Treelets are numbered in node (BFS) order of their roots.
+    const int64_t fit = (treelet_bytes - 16 - h->root_bytes) / h->rec_bytes + 1;
+    std::vector<int64_t> carry(nn, 1);
+    for (int64_t x = nn - 1; x >= 0; --x) {
+      const Node &nd = nodes[x];
+      int64_t c = 1;
+      for (int i = 0; i < nd.count; ++i) c += carry[nd.first + i];
+      if (c <= fit)
+        carry[x] = c;
+      else
+        ext[x] = 1;
+    }
+    std::vector<int32_t> tl_of(nn, -1);
+    tl_of[0] = 0;
+    for (int64_t x = 1; x < nn; ++x)
+      if (ext[nodes[x].parent]) {
+        tl_of[x] = (int32_t)roots.size();
+        roots.push_back((int32_t)x);
+      }
+    members.resize(roots.size());
+    for (size_t t = 0; t < roots.size(); ++t) {
+      std::vector<int32_t> &mem = members[t];
+      mem.push_back(roots[t]);
+      for (size_t i = 0; i < mem.size(); ++i) {
+        const int32_t x = mem[i];
+        tlet[x] = (int32_t)t;
+        local[x] = (int32_t)i;
+        const Node &nd = nodes[x];
+        if (ext[x])
+          child_tlet[x] = tl_of[nd.first];
+        else
+          for (int c = 0; c < nd.count; ++c) mem.push_back(nd.first + c);
+      }
+    }
+  } else {
+    // Top-down: greedy BFS from each root adding whole sibling groups inside the budget; a
+    // group that does not fit makes each of its nodes a new treelet root, numbered in the
+    // order of creation.
+    for (size_t t = 0; t < roots.size(); ++t) {
+      std::vector<int32_t> mem{roots[t]};
+      tlet[roots[t]] = (int32_t)t;
+      local[roots[t]] = 0;
+      int64_t used_bytes = 16 + h->root_bytes;
+      for (size_t i = 0; i < mem.size(); ++i) {  // `mem` doubles as the BFS queue
+        const Node &nd = nodes[mem[i]];
+        if (nd.count == 0) continue;
+        int64_t need = (int64_t)nd.count * h->rec_bytes;
+        if (used_bytes + need <= treelet_bytes) {
+          used_bytes += need;
+          for (int c = 0; c < nd.count; ++c) {
+            tlet[nd.first + c] = (int32_t)t;
+            local[nd.first + c] = (int32_t)mem.size();
+            mem.push_back(nd.first + c);
+          }
+        } else {
+          ext[mem[i]] = 1;
+          child_tlet[mem[i]] = (int32_t)roots.size();
+          for (int c = 0; c < nd.count; ++c) roots.push_back(nd.first + c);
+        }
+      }
+      members.push_back(std::move(mem));
+    }
+  }
+  const int64_t ntl = (int64_t)roots.size();
+  size_t maxn = 1;
+  for (auto &mm : members) maxn = std::max(maxn, mm.size());
+  if (maxn > 65535) {
+    return cbvh::fail(CBVH_ERR_ARG, "too many nodes in one treelet");
+  }
+  while (((size_t)1 << h->lbits) < maxn) ++h->lbits;
+  if (h->lbits < 32 && (uint64_t)ntl >= ((uint64_t)1 << (32 - h->lbits))) {
+    return cbvh::fail(CBVH_ERR_ARG, "too many treelets for 32-bit node references; use larger treelets");
+  }
 
-extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_t *tris_host, int64_t n_tris, int k,
-                          int branching, int quant_bits, int treelet_bytes, cbvh_bvh **out) {
-  cbvh::clear_error();
-  if (!out) return cbvh::fail(CBVH_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (!verts_host || !tris_host) return cbvh::fail(CBVH_ERR_ARG, "NULL mesh pointer");
+  // ---- predictor-corrector encoding, top-down (parents precede children in BFS) ----
+  std::vector<int32_t> dec((size_t)nn * K * 2);
+  std::vector<uint16_t> corr((size_t)nn * K * 2, 0);
+  const uint32_t dmax = quant_bits ? (1u << quant_bits) - 1 : 0;
+  for (int64_t x = 0; x < nn; ++x) {
+    const int32_t *C = &lat[(size_t)x * K * 2];
+    int32_t *D = &dec[(size_t)x * K * 2];
+    if (local[x] == 0 || quant_bits == 0 || quant_bits == CBVH_QUANT_FP16) {
+      std::copy(C, C + 2 * K, D);
+      continue;
+    }
+    const int32_t *P = &dec[(size_t)nodes[x].parent * K * 2];
+    for (int j = 0; j < K; ++j) {
+      uint32_t range = (uint32_t)((int64_t)P[2 * j + 1] - P[2 * j]);
+      int s = 0;
+      while ((range >> s) > dmax) ++s;
+      uint32_t dl = (uint32_t)((int64_t)C[2 * j] - P[2 * j]) >> s;
+      uint32_t dh = (uint32_t)((int64_t)P[2 * j + 1] - C[2 * j + 1]) >> s;
+      corr[(size_t)x * K * 2 + 2 * j] = (uint16_t)dl;
+      corr[(size_t)x * K * 2 + 2 * j + 1] = (uint16_t)dh;
+      D[2 * j] = (int32_t)((int64_t)P[2 * j] + ((int64_t)dl << s));
+      D[2 * j + 1] = (int32_t)((int64_t)P[2 * j + 1] - ((int64_t)dh << s));
+    }
+  }
+
+  // ---- serialise ----
+  std::vector<int64_t> toff(ntl + 1);
+  int64_t pos = (64 + 8 * (ntl + 1) + 15) / 16 * 16;
+  h->off_treelets = pos;
+  for (int64_t t = 0; t < ntl; ++t) {
+    toff[t] = pos;
+    pos += (16 + h->root_bytes + (int64_t)(members[t].size() - 1) * h->rec_bytes + 15) / 16 * 16;
+  }
+  toff[ntl] = pos;
+  h->off_tris = pos;
+  const int64_t total = pos + 48 * n_tris;
+  std::vector<uint8_t> &b = h->blob;
+  b.assign(total, 0);
+  int max_td = 0;
+  std::vector<int32_t> leaf_slot(nn, -1), slot_tri;
+  slot_tri.reserve(n_tris);
+  for (int64_t x = 0; x < nn; ++x)
+    if (nodes[x].count == 0) {
+      leaf_slot[x] = (int32_t)slot_tri.size();
+      slot_tri.push_back(nodes[x].tri);
+    }
+  int64_t first_node = 0;
+  for (int64_t t = 0; t < ntl; ++t) {
+    const auto &mem = members[t];
+    const int64_t T0 = toff[t];
+    w32(b, T0, (uint32_t)mem.size());
+    w32(b, T0 + 4, (uint32_t)first_node);
+    first_node += (int64_t)mem.size();
+    std::vector<int> tdepth(mem.size(), 0);
+    for (size_t l = 0; l < mem.size(); ++l) {
+      const int32_t x = mem[l];
+      const Node &nd = nodes[x];
+      if (l) tdepth[l] = tdepth[local[nd.parent]] + 1;
+      max_td = std::max(max_td, tdepth[l]);
+      const int64_t R = T0 + 16 + (l ? h->root_bytes + (int64_t)(l - 1) * h->rec_bytes : 0);
+      uint32_t w0 = (l ? (uint32_t)local[nd.parent] : 0xFFFFu) | ((uint32_t)nd.count << 16) |
+                    ((uint32_t)ext[x] << 21) | ((uint32_t)tdepth[l] << 24);
+      uint32_t w1 = nd.count == 0 ? (uint32_t)leaf_slot[x]
+                                  : (ext[x] ? (uint32_t)child_tlet[x] : (uint32_t)local[nd.first]);
+      w32(b, R, w0);
+      w32(b, R + 4, w1);
+      const int32_t *D = &dec[(size_t)x * K * 2];
+      for (int j = 0; j < K; ++j) {
+        if (quant_bits == 0) {
+          w32(b, R + 8 + 8 * j, f32_bits(to_f32_down(D[2 * j], h->e)));
+          w32(b, R + 12 + 8 * j, f32_bits(to_f32_up(D[2 * j + 1], h->e)));
+        } else if (quant_bits == CBVH_QUANT_FP16) {  // exact lattice values, rounded outward to half
+          w16(b, R + 8 + 4 * j, half_down(std::ldexp((double)D[2 * j], h->e)));
+          w16(b, R + 10 + 4 * j, half_up(std::ldexp((double)D[2 * j + 1], h->e)));
+        } else if (l == 0) {
+          w32(b, R + 8 + 8 * j, (uint32_t)D[2 * j]);
+          w32(b, R + 12 + 8 * j, (uint32_t)D[2 * j + 1]);
+        } else if (quant_bits == 8) {
+          b[R + 8 + 2 * j] = (uint8_t)corr[(size_t)x * K * 2 + 2 * j];
+          b[R + 9 + 2 * j] = (uint8_t)corr[(size_t)x * K * 2 + 2 * j + 1];
+        } else {
+          w16(b, R + 8 + 4 * j, corr[(size_t)x * K * 2 + 2 * j]);
+          w16(b, R + 10 + 4 * j, corr[(size_t)x * K * 2 + 2 * j + 1]);
+        }
+      }
+    }
+  }
+  if (verts_host) {
+    for (int64_t i = 0; i < n_tris; ++i) {
+      const int64_t P = h->off_tris + 48 * i;
+      const int32_t t = slot_tri[i];
+      for (int c = 0; c < 3; ++c)
+        for (int x = 0; x < 3; ++x) w32(b, P + 16 * c + 4 * x, f32_bits(verts_host[3 * (int64_t)tris_host[3 * (int64_t)t + c] + x]));
+      w32(b, P + 12, (uint32_t)t);
+    }
+  } else {  // a plan: the table stays zero; slot_tri holds each leaf's position in the order
+    h->leaf_pos = std::move(slot_tri);
+  }
+  h->max_tdepth = max_td;
+  h->n_tris = n_tris;
+  h->n_nodes = nn;
+  h->n_treelets = ntl;
+  // header
+  w32(b, 0, 0x48564243u);
+  w16(b, 4, 1);
+  b[6] = (uint8_t)k;
+  b[7] = (uint8_t)K;
+  b[8] = (uint8_t)branching;
+  b[9] = (uint8_t)quant_bits;
+  b[10] = (uint8_t)h->lbits;
+  b[11] = (uint8_t)max_td;
+  w32(b, 12, (uint32_t)h->e);
+  w32(b, 16, (uint32_t)n_tris);
+  w32(b, 20, (uint32_t)nn);
+  w32(b, 24, (uint32_t)ntl);
+  w32(b, 28, (uint32_t)h->rec_bytes);
+  w32(b, 32, (uint32_t)h->root_bytes);
+  w32(b, 36, (uint32_t)treelet_bytes);
+  w32(b, 40, (uint32_t)h->depth);
+  w32(b, 44, (uint32_t)packing);
+  w64(b, 48, (uint64_t)h->off_tris);
+  w64(b, 56, (uint64_t)total);
+  for (int64_t t = 0; t <= ntl; ++t) w64(b, 64 + 8 * t, (uint64_t)toff[t]);
+  return CBVH_OK;
+}
+
+// Validated parameters and record sizes of a new handle (no mesh data yet).
+int new_handle(int64_t n_verts, int64_t n_tris, int k, int branching, int quant_bits, int treelet_bytes,
+               cbvh_bvh **out) {
   if (k != 6 && k != 18 && k != 24 && k != 26) return cbvh::fail(CBVH_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (branching != 2 && branching != 4 && branching != 8 && branching != 16)
     return cbvh::fail(CBVH_ERR_ARG, "branching must be 2, 4, 8 or 16");
@@ -247,13 +462,13 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
   if (n_tris < 1 || n_tris > 0x7fffffff || n_verts < 3 || n_verts > 0x7fffffff)
     return cbvh::fail(CBVH_ERR_MESH, "mesh size out of range");
 
+  const int K = k / 2;
   auto h = new cbvh_bvh();
   h->k = k;
-  h->K = k / 2;
+  h->K = K;
   h->m = branching;
   h->bits = quant_bits;
   h->treelet_bytes = treelet_bytes;
-  const int K = h->K;
   if (quant_bits == CBVH_QUANT_FP16) {  // absolute half-precision bounds in every record
     h->root_bytes = h->rec_bytes = 8 + 4 * K;
   } else {
@@ -264,6 +479,24 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
     delete h;
     return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes too small for one sibling group");
   }
+  h->n_tris = n_tris;
+  h->n_verts = n_verts;
+  *out = h;
+  return CBVH_OK;
+}
+
+
+}  // namespace
+
+extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_t *tris_host, int64_t n_tris, int k,
+                          int branching, int quant_bits, int treelet_bytes, cbvh_bvh **out) {
+  cbvh::clear_error();
+  if (!out) return cbvh::fail(CBVH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!verts_host || !tris_host) return cbvh::fail(CBVH_ERR_ARG, "NULL mesh pointer");
+  cbvh_bvh *h = nullptr;
+  if (int rc = new_handle(n_verts, n_tris, k, branching, quant_bits, treelet_bytes, &h)) return rc;
+  const int K = h->K;
 
   Builder B{k, K, branching, quant_bits, treelet_bytes, verts_host, n_verts, tris_host, n_tris};
   for (int64_t i = 0; i < 3 * n_verts; ++i)
@@ -367,7 +600,6 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
       }
     }
   }
-  for (const Node &nd : B.nodes) h->depth = std::max(h->depth, nd.depth);
   if (quant_bits == CBVH_QUANT_FP16)  // every bound lies inside the root's: check the root
     for (int j = 0; j < 2 * K; ++j)
       if (std::fabs(std::ldexp((double)lat[j], h->e)) > 65504.0) {
@@ -375,211 +607,34 @@ extern "C" int cbvh_build(const float *verts_host, int64_t n_verts, const int32_
         return cbvh::fail(CBVH_ERR_MESH, "mesh bounds exceed the half-precision range (+-65504) of quant_bits = 1");
       }
 
-  // ---- treelets ----
-  std::vector<int32_t> tlet(nn), local(nn), child_tlet(nn, -1);
-  std::vector<uint8_t> ext(nn, 0);
-  std::vector<int32_t> roots{0};
-  std::vector<std::vector<int32_t>> members;
-  const int packing = cbvh::treelet_packing();
-  if (packing == CBVH_PACK_BOTTOM_UP) {
-    // Bottom-up: `carry` counts the nodes of a subtree not yet cut off.  A node keeps its
-    // children while it and everything they carry fit one treelet; else every child roots
-    // a treelet of its own.  Treelets are numbered in node (BFS) order of their roots.
-    const int64_t fit = (treelet_bytes - 16 - h->root_bytes) / h->rec_bytes + 1;
-    std::vector<int64_t> carry(nn, 1);
-    for (int64_t x = nn - 1; x >= 0; --x) {
-      const Node &nd = B.nodes[x];
-      int64_t c = 1;
-      for (int i = 0; i < nd.count; ++i) c += carry[nd.first + i];
-      if (c <= fit)
-        carry[x] = c;
-      else
-        ext[x] = 1;
-    }
-    std::vector<int32_t> tl_of(nn, -1);
-    tl_of[0] = 0;
-    for (int64_t x = 1; x < nn; ++x)
-      if (ext[B.nodes[x].parent]) {
-        tl_of[x] = (int32_t)roots.size();
-        roots.push_back((int32_t)x);
-      }
-    members.resize(roots.size());
-    for (size_t t = 0; t < roots.size(); ++t) {
-      std::vector<int32_t> &mem = members[t];
-      mem.push_back(roots[t]);
-      for (size_t i = 0; i < mem.size(); ++i) {
-        const int32_t x = mem[i];
-        tlet[x] = (int32_t)t;
-        local[x] = (int32_t)i;
-        const Node &nd = B.nodes[x];
-        if (ext[x])
-          child_tlet[x] = tl_of[nd.first];
-        else
-          for (int c = 0; c < nd.count; ++c) mem.push_back(nd.first + c);
-      }
-    }
-  } else {
-    // Top-down: greedy BFS from each root adding whole sibling groups inside the budget; a
-    // group that does not fit makes each of its nodes a new treelet root, numbered in the
-    // order of creation.
-    for (size_t t = 0; t < roots.size(); ++t) {
-      std::vector<int32_t> mem{roots[t]};
-      tlet[roots[t]] = (int32_t)t;
-      local[roots[t]] = 0;
-      int64_t used_bytes = 16 + h->root_bytes;
-      for (size_t i = 0; i < mem.size(); ++i) {  // `mem` doubles as the BFS queue
-        const Node &nd = B.nodes[mem[i]];
-        if (nd.count == 0) continue;
-        int64_t need = (int64_t)nd.count * h->rec_bytes;
-        if (used_bytes + need <= treelet_bytes) {
-          used_bytes += need;
-          for (int c = 0; c < nd.count; ++c) {
-            tlet[nd.first + c] = (int32_t)t;
-            local[nd.first + c] = (int32_t)mem.size();
-            mem.push_back(nd.first + c);
-          }
-        } else {
-          ext[mem[i]] = 1;
-          child_tlet[mem[i]] = (int32_t)roots.size();
-          for (int c = 0; c < nd.count; ++c) roots.push_back(nd.first + c);
-        }
-      }
-      members.push_back(std::move(mem));
-    }
-  }
-  const int64_t ntl = (int64_t)roots.size();
-  size_t maxn = 1;
-  for (auto &mm : members) maxn = std::max(maxn, mm.size());
-  if (maxn > 65535) {
+  h->headroom = E.headroom;
+  if (int rc = layout(h, B.nodes, lat, verts_host, tris_host, n_tris)) {
     delete h;
-    return cbvh::fail(CBVH_ERR_ARG, "too many nodes in one treelet");
+    return rc;
   }
-  while (((size_t)1 << h->lbits) < maxn) ++h->lbits;
-  if (h->lbits < 32 && (uint64_t)ntl >= ((uint64_t)1 << (32 - h->lbits))) {
-    delete h;
-    return cbvh::fail(CBVH_ERR_ARG, "too many treelets for 32-bit node references; use larger treelets");
-  }
-
-  // ---- predictor-corrector encoding, top-down (parents precede children in BFS) ----
-  std::vector<int32_t> dec((size_t)nn * K * 2);
-  std::vector<uint16_t> corr((size_t)nn * K * 2, 0);
-  const uint32_t dmax = quant_bits ? (1u << quant_bits) - 1 : 0;
-  for (int64_t x = 0; x < nn; ++x) {
-    const int32_t *C = &lat[(size_t)x * K * 2];
-    int32_t *D = &dec[(size_t)x * K * 2];
-    if (local[x] == 0 || quant_bits == 0 || quant_bits == CBVH_QUANT_FP16) {
-      std::copy(C, C + 2 * K, D);
-      continue;
-    }
-    const int32_t *P = &dec[(size_t)B.nodes[x].parent * K * 2];
-    for (int j = 0; j < K; ++j) {
-      uint32_t range = (uint32_t)((int64_t)P[2 * j + 1] - P[2 * j]);
-      int s = 0;
-      while ((range >> s) > dmax) ++s;
-      uint32_t dl = (uint32_t)((int64_t)C[2 * j] - P[2 * j]) >> s;
-      uint32_t dh = (uint32_t)((int64_t)P[2 * j + 1] - C[2 * j + 1]) >> s;
-      corr[(size_t)x * K * 2 + 2 * j] = (uint16_t)dl;
-      corr[(size_t)x * K * 2 + 2 * j + 1] = (uint16_t)dh;
-      D[2 * j] = (int32_t)((int64_t)P[2 * j] + ((int64_t)dl << s));
-      D[2 * j + 1] = (int32_t)((int64_t)P[2 * j + 1] - ((int64_t)dh << s));
-    }
-  }
-
-  // ---- serialise ----
-  std::vector<int64_t> toff(ntl + 1);
-  int64_t pos = (64 + 8 * (ntl + 1) + 15) / 16 * 16;
-  h->off_treelets = pos;
-  for (int64_t t = 0; t < ntl; ++t) {
-    toff[t] = pos;
-    pos += (16 + h->root_bytes + (int64_t)(members[t].size() - 1) * h->rec_bytes + 15) / 16 * 16;
-  }
-  toff[ntl] = pos;
-  h->off_tris = pos;
-  const int64_t total = pos + 48 * n_tris;
-  std::vector<uint8_t> &b = h->blob;
-  b.assign(total, 0);
-  int max_td = 0;
-  std::vector<int32_t> leaf_slot(nn, -1), slot_tri;
-  slot_tri.reserve(n_tris);
-  for (int64_t x = 0; x < nn; ++x)
-    if (B.nodes[x].count == 0) {
-      leaf_slot[x] = (int32_t)slot_tri.size();
-      slot_tri.push_back(B.nodes[x].tri);
-    }
-  int64_t first_node = 0;
-  for (int64_t t = 0; t < ntl; ++t) {
-    const auto &mem = members[t];
-    const int64_t T0 = toff[t];
-    w32(b, T0, (uint32_t)mem.size());
-    w32(b, T0 + 4, (uint32_t)first_node);
-    first_node += (int64_t)mem.size();
-    std::vector<int> tdepth(mem.size(), 0);
-    for (size_t l = 0; l < mem.size(); ++l) {
-      const int32_t x = mem[l];
-      const Node &nd = B.nodes[x];
-      if (l) tdepth[l] = tdepth[local[nd.parent]] + 1;
-      max_td = std::max(max_td, tdepth[l]);
-      const int64_t R = T0 + 16 + (l ? h->root_bytes + (int64_t)(l - 1) * h->rec_bytes : 0);
-      uint32_t w0 = (l ? (uint32_t)local[nd.parent] : 0xFFFFu) | ((uint32_t)nd.count << 16) |
-                    ((uint32_t)ext[x] << 21) | ((uint32_t)tdepth[l] << 24);
-      uint32_t w1 = nd.count == 0 ? (uint32_t)leaf_slot[x]
-                                  : (ext[x] ? (uint32_t)child_tlet[x] : (uint32_t)local[nd.first]);
-      w32(b, R, w0);
-      w32(b, R + 4, w1);
-      const int32_t *D = &dec[(size_t)x * K * 2];
-      for (int j = 0; j < K; ++j) {
-        if (quant_bits == 0) {
-          w32(b, R + 8 + 8 * j, f32_bits(to_f32_down(D[2 * j], h->e)));
-          w32(b, R + 12 + 8 * j, f32_bits(to_f32_up(D[2 * j + 1], h->e)));
-        } else if (quant_bits == CBVH_QUANT_FP16) {  // exact lattice values, rounded outward to half
-          w16(b, R + 8 + 4 * j, half_down(std::ldexp((double)D[2 * j], h->e)));
-          w16(b, R + 10 + 4 * j, half_up(std::ldexp((double)D[2 * j + 1], h->e)));
-        } else if (l == 0) {
-          w32(b, R + 8 + 8 * j, (uint32_t)D[2 * j]);
-          w32(b, R + 12 + 8 * j, (uint32_t)D[2 * j + 1]);
-        } else if (quant_bits == 8) {
-          b[R + 8 + 2 * j] = (uint8_t)corr[(size_t)x * K * 2 + 2 * j];
-          b[R + 9 + 2 * j] = (uint8_t)corr[(size_t)x * K * 2 + 2 * j + 1];
-        } else {
-          w16(b, R + 8 + 4 * j, corr[(size_t)x * K * 2 + 2 * j]);
-          w16(b, R + 10 + 4 * j, corr[(size_t)x * K * 2 + 2 * j + 1]);
-        }
-      }
-    }
-  }
-  for (int64_t i = 0; i < n_tris; ++i) {
-    const int64_t P = h->off_tris + 48 * i;
-    const int32_t t = slot_tri[i];
-    for (int c = 0; c < 3; ++c)
-      for (int x = 0; x < 3; ++x) w32(b, P + 16 * c + 4 * x, f32_bits(verts_host[3 * (int64_t)tris_host[3 * (int64_t)t + c] + x]));
-    w32(b, P + 12, (uint32_t)t);
-  }
-  h->max_tdepth = max_td;
-  h->n_tris = n_tris;
   h->n_verts = n_verts;
-  h->n_nodes = nn;
-  h->n_treelets = ntl;
-  // header
-  w32(b, 0, 0x48564243u);
-  w16(b, 4, 1);
-  b[6] = (uint8_t)k;
-  b[7] = (uint8_t)K;
-  b[8] = (uint8_t)branching;
-  b[9] = (uint8_t)quant_bits;
-  b[10] = (uint8_t)h->lbits;
-  b[11] = (uint8_t)max_td;
-  w32(b, 12, (uint32_t)h->e);
-  w32(b, 16, (uint32_t)n_tris);
-  w32(b, 20, (uint32_t)nn);
-  w32(b, 24, (uint32_t)ntl);
-  w32(b, 28, (uint32_t)h->rec_bytes);
-  w32(b, 32, (uint32_t)h->root_bytes);
-  w32(b, 36, (uint32_t)treelet_bytes);
-  w32(b, 40, (uint32_t)h->depth);
-  w32(b, 44, (uint32_t)packing);
-  w64(b, 48, (uint64_t)h->off_tris);
-  w64(b, 56, (uint64_t)total);
-  for (int64_t t = 0; t <= ntl; ++t) w64(b, 64 + 8 * t, (uint64_t)toff[t]);
+  h->geometry = true;
+  *out = h;
+  return CBVH_OK;
+}
+
+extern "C" int cbvh_build_plan(int64_t n_verts, int64_t n_tris, int k, int branching, int quant_bits,
+                               int treelet_bytes, cbvh_bvh **out) {
+  cbvh::clear_error();
+  if (!out) return cbvh::fail(CBVH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  cbvh_bvh *h = nullptr;
+  if (int rc = new_handle(n_verts, n_tris, k, branching, quant_bits, treelet_bytes, &h)) return rc;
+  // the tree's shape depends on n_tris and the branching alone: split nothing, keep positions
+  Builder B{k, h->K, branching, quant_bits, treelet_bytes, nullptr, n_verts, nullptr, n_tris};
+  B.build_tree(true);
+  const std::vector<int32_t> lat((size_t)B.nodes.size() * h->K * 2, 0);
+  if (int rc = layout(h, B.nodes, lat, nullptr, nullptr, n_tris)) {
+    delete h;
+    return rc;
+  }
+  h->headroom = cbvh::lattice_headroom();
+  h->geometry = false;
   *out = h;
   return CBVH_OK;
 }
@@ -611,6 +666,8 @@ extern "C" int cbvh_info(const cbvh_bvh *h, cbvh_info_t *o) {
 extern "C" int cbvh_blob_host(const cbvh_bvh *h, const uint8_t **blob, int64_t *bytes) {
   cbvh::clear_error();
   if (!h || !blob || !bytes) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  if (h->host_stale)
+    return cbvh::fail(CBVH_ERR_STATE, "host blob not updated by the device build (CBVH_BUILD_HOST_COPY not given)");
   *blob = h->blob.data();
   *bytes = (int64_t)h->blob.size();
   return CBVH_OK;

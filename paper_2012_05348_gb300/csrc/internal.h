@@ -25,6 +25,17 @@ struct cbvh_bvh {
   // and the workspace holding the plan's device arrays
   std::vector<int64_t> refit_level_start, refit_td_start;
   void *refit_ws = nullptr;
+  // lattice bits kept free by the build (CBVH_OPT_LATTICE_HEADROOM at build or plan time)
+  int headroom = 0;
+  // false for a plan (cbvh_build_plan) until its first cbvh_build_device: the blob holds the
+  // tree's shape, zero bounds and an empty triangle table
+  bool geometry = true;
+  // plan: position in the median-split order of each leaf slot's triangle
+  std::vector<int32_t> leaf_pos;
+  // the host blob lags the device blob (a device build without CBVH_BUILD_HOST_COPY)
+  bool host_stale = false;
+  // workspace holding the device build's plan arrays (cbvh_build_device)
+  void *devbuild_ws = nullptr;
 };
 
 namespace cbvh {
@@ -39,4 +50,10 @@ void set_lattice_headroom(int bits);
 int lattice_headroom();
 // Adds to the process-wide count of kernels launched (cbvh_kernel_launches).
 void count_launches(int n);
+// Workspace bytes of the refit plan and scratch (the front of a device-build workspace).
+int64_t refit_workspace_total(const cbvh_bvh *h);
+// The refit kernels (bounds bottom-up, encoding top-down) for lattice exponent h->e on
+// `stream`, reporting into the device int32 `status`; adds to `launches`.
+int refit_launch(cbvh_bvh *h, const float *verts_dev, const int32_t *tris_dev, uint8_t *workspace,
+                 int32_t *status, void *stream, int &launches);
 }  // namespace cbvh

@@ -1714,6 +1714,8 @@ int launch_single(Params &p, uint8_t *ws, const WsPlan &w, int sms, cudaStream_t
 int check_pair(const cbvh_bvh *A, const cbvh_bvh *B) {
   if (!A || !B) return cbvh::fail(CBVH_ERR_ARG, "NULL handle");
   if (!A->dev_blob || !B->dev_blob) return cbvh::fail(CBVH_ERR_STATE, "handle has no device blob; call cbvh_attach");
+  if (!A->geometry || !B->geometry)
+    return cbvh::fail(CBVH_ERR_STATE, "hierarchy has no geometry (a plan before a successful cbvh_build_device)");
   return CBVH_OK;
 }
 
@@ -1736,6 +1738,8 @@ extern "C" int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *str
   cbvh::clear_error();
   if (!h || !dev_blob) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   if (bytes < (int64_t)h->blob.size()) return cbvh::fail(CBVH_ERR_ARG, "device buffer smaller than the blob");
+  if (h->host_stale)
+    return cbvh::fail(CBVH_ERR_STATE, "host blob not updated by the device build (CBVH_BUILD_HOST_COPY not given)");
   if (reinterpret_cast<uintptr_t>(dev_blob) & 255) return cbvh::fail(CBVH_ERR_ARG, "device buffer not 256-byte aligned");
   cudaError_t e = cudaMemcpyAsync(dev_blob, h->blob.data(), h->blob.size(), cudaMemcpyHostToDevice,
                                   static_cast<cudaStream_t>(stream));

@@ -1,0 +1,56 @@
+// Exact lattice arithmetic shared by the device refit and the device build: the slab
+// directions and floor / ceil of d_j . v / 2^e for FP32 vertices, decided exactly in FP64.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace {
+
+__constant__ int c_rdir[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
+                                  {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                  {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
+
+constexpr int64_t kLatLimit = int64_t(1) << 30;
+
+// ---------------------------------------------------------------- exact lattice values
+// a + b exactly as s + err (Knuth's TwoSum; FP64, round to nearest, no contraction).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &err) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// floor(a + b + c) of the exact real sum.  Grow-Expansion (Shewchuk 1997) turns (a, b, c)
+// into a non-overlapping expansion q2 > q1 > q0 (by magnitude): if q2 has a fractional part,
+// the smaller components cannot move the sum across an integer, so the floor is q2's; if q2
+// is an integer the same holds one component down.
+__device__ long long floor3_exact(double a, double b, double c) {
+  // fast path: the rounded sum is off by at most 2u (|a| + |b| + |c|) (two additions, u =
+  // 2^-53); when twice that margin cannot reach an integer, its floor is the exact floor
+  const double sum = __dadd_rn(__dadd_rn(a, b), c);
+  const double slack = (fabs(a) + fabs(b) + fabs(c)) * 0x1p-51;
+  const double fl = floor(__dsub_rn(sum, slack));
+  if (fl == floor(__dadd_rn(sum, slack))) return (long long)fl;
+  double x1, y1;
+  two_sum(a, b, x1, y1);  // expansion [y1, x1]
+  double q, q0, q1, q2;
+  two_sum(c, y1, q, q0);
+  two_sum(q, x1, q2, q1);  // expansion [q0, q1, q2]
+  const double f2 = floor(q2);
+  if (f2 != q2) return (long long)f2;
+  const double f1 = floor(q1);
+  if (f1 != q1) return (long long)q2 + (long long)f1;
+  return (long long)q2 + (long long)q1 + (long long)floor(q0);
+}
+
+// Lattice interval [floor, ceil] of d_j . v / 2^e for an FP32 vertex.
+__device__ __forceinline__ void lattice_of(const float *v, int j, double inv, long long &lo, long long &hi) {
+  double t[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) t[c] = (double)c_rdir[j][c] * ((double)v[c] * inv);  // exact: scaling by 2^-e
+  lo = floor3_exact(t[0], t[1], t[2]);
+  hi = -floor3_exact(-t[0], -t[1], -t[2]);
+}
+
+}  // namespace

@@ -27,54 +27,9 @@
 #include <vector>
 
 #include "internal.h"
+#include "lattice.cuh"
 
 namespace {
-
-__constant__ int c_rdir[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
-                                  {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
-                                  {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
-
-constexpr int64_t kLatLimit = int64_t(1) << 30;
-
-// ---------------------------------------------------------------- exact lattice values
-// a + b exactly as s + err (Knuth's TwoSum; FP64, round to nearest, no contraction).
-__device__ __forceinline__ void two_sum(double a, double b, double &s, double &err) {
-  s = __dadd_rn(a, b);
-  const double bb = __dsub_rn(s, a);
-  err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-}
-
-// floor(a + b + c) of the exact real sum.  Grow-Expansion (Shewchuk 1997) turns (a, b, c)
-// into a non-overlapping expansion q2 > q1 > q0 (by magnitude): if q2 has a fractional part,
-// the smaller components cannot move the sum across an integer, so the floor is q2's; if q2
-// is an integer the same holds one component down.
-__device__ long long floor3_exact(double a, double b, double c) {
-  // fast path: the rounded sum is off by at most 2u (|a| + |b| + |c|) (two additions, u =
-  // 2^-53); when twice that margin cannot reach an integer, its floor is the exact floor
-  const double sum = __dadd_rn(__dadd_rn(a, b), c);
-  const double slack = (fabs(a) + fabs(b) + fabs(c)) * 0x1p-51;
-  const double fl = floor(__dsub_rn(sum, slack));
-  if (fl == floor(__dadd_rn(sum, slack))) return (long long)fl;
-  double x1, y1;
-  two_sum(a, b, x1, y1);  // expansion [y1, x1]
-  double q, q0, q1, q2;
-  two_sum(c, y1, q, q0);
-  two_sum(q, x1, q2, q1);  // expansion [q0, q1, q2]
-  const double f2 = floor(q2);
-  if (f2 != q2) return (long long)f2;
-  const double f1 = floor(q1);
-  if (f1 != q1) return (long long)q2 + (long long)f1;
-  return (long long)q2 + (long long)q1 + (long long)floor(q0);
-}
-
-// Lattice interval [floor, ceil] of d_j . v / 2^e for an FP32 vertex.
-__device__ __forceinline__ void lattice_of(const float *v, int j, double inv, long long &lo, long long &hi) {
-  double t[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) t[c] = (double)c_rdir[j][c] * ((double)v[c] * inv);  // exact: scaling by 2^-e
-  lo = floor3_exact(t[0], t[1], t[2]);
-  hi = -floor3_exact(-t[0], -t[1], -t[2]);
-}
 
 // ---------------------------------------------------------------- outward roundings
 // Largest half <= v (down) or smallest half >= v (up), IEEE binary16 bits, for finite v:
@@ -409,17 +364,28 @@ extern "C" int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, 
   const RefitLayout L = refit_layout(h);
   if (workspace_bytes < L.total) return cbvh::fail(CBVH_ERR_WORKSPACE, "refit workspace too small");
   if (n_verts != h->n_verts) return cbvh::fail(CBVH_ERR_ARG, "a refit needs the build's vertex count");
-  uint8_t *ws = static_cast<uint8_t *>(workspace);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  int launches = 0;
+  const int rc = cbvh::refit_launch(h, verts_dev, tris_dev, static_cast<uint8_t *>(workspace), status, stream, launches);
+  cbvh::count_launches(launches);
+  return rc;
+}
+
+namespace cbvh {
+int64_t refit_workspace_total(const cbvh_bvh *h) { return refit_layout(h).total; }
+
+int refit_launch(cbvh_bvh *h, const float *verts_dev, const int32_t *tris_dev, uint8_t *ws, int32_t *status,
+                 void *stream, int &launches) {
+  const RefitLayout L = refit_layout(h);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   RefitArgs a;
   std::memset(&a, 0, sizeof a);
   a.blob = static_cast<uint8_t *>(h->dev_blob);
   a.off_tris = h->off_tris;
   a.verts = verts_dev;
   a.tris = tris_dev;
-  a.n_verts = n_verts;
+  a.n_verts = h->n_verts;
   a.n_tris = h->n_tris;
   a.K = h->K;
   a.bits = h->bits;
@@ -436,9 +402,9 @@ extern "C" int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, 
   a.VL = reinterpret_cast<int32_t *>(ws + L.VL);
   const int64_t nC = 2 * h->n_nodes * h->K;
   init_bounds<<<(unsigned)std::min<int64_t>((nC + 255) / 256, 4096), 256, 0, s>>>(a.C, nC);
-  int launches = 1;
+  launches += 1;
   auto grid = [](int64_t items) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 65535)); };
-  vertex_lattice<<<grid(n_verts * h->K), 256, 0, s>>>(a);
+  vertex_lattice<<<grid(h->n_verts * h->K), 256, 0, s>>>(a);
   ++launches;
   a.order = reinterpret_cast<const int32_t *>(ws + L.by_level);
   const auto &ls = h->refit_level_start;
@@ -460,7 +426,7 @@ extern "C" int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, 
       ++launches;
     }
   }
-  cbvh::count_launches(launches);
-  e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "refit launch");
 }
+}  // namespace cbvh

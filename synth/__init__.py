@@ -8,7 +8,7 @@ seeded NumPy PCG64 stream, computing in FP64 and rounding the results to FP32.
 The paper measures on the OpenCollBench models (ds9 station, hand, robots; Sec. IV and
 Fig. 2), which are not available here.  Displaced icospheres, a fractal heightfield,
 random boxes and a DH serial arm stand in for them, at the sizes of the five workloads
-described in DESIGN.md.
+generated by C1 to C5 below.
 
 Pose convention: a pose is 12 FP32 numbers, the row-major 3x3 rotation R followed by the
 translation t, and maps a point of mesh B into the frame of mesh A: x_A = R x_B + t.
