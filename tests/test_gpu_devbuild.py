@@ -46,7 +46,7 @@ MESHES = {
     "ragged_unused": lambda: (synth.icosphere(3, 1.0, 0.15, seed=3)[0], synth.icosphere(3, 1.0, 0.15, seed=3)[1][:1111]),
     "one": lambda: (synth.icosphere(1)[0], synth.icosphere(1)[1][:1]),
     "three": lambda: (synth.icosphere(1)[0], synth.icosphere(1)[1][5:8]),
-    "tiny_scale": lambda: ((synth.icosphere(2, 1.0, 0.1, seed=1)[0] * np.float32(1e-30)).astype(np.float32),
+    "tiny_scale": lambda: ((synth.icosphere(2, 1.0, 0.1, seed=1)[0] * np.float32(1e-25)).astype(np.float32),
                            synth.icosphere(2, 1.0, 0.1, seed=1)[1]),
     "huge_scale": lambda: ((synth.icosphere(2, 1.0, 0.1, seed=1)[0] * np.float32(3e20)).astype(np.float32),
                            synth.icosphere(2, 1.0, 0.1, seed=1)[1]),
@@ -165,6 +165,7 @@ def test_device_build_errors(cb):
     bad = v.copy()
     bad[3, 1] = np.inf
     refused(bad, t)
+    refused((v * np.float32(1e-30)).astype(np.float32), t)  # lattice exponent below its range
     h16 = cb.BVH.plan(len(v), len(t), 18, 4, 1, 4096)
     refused((v * 70000.0).astype(np.float32), t, h16)  # beyond the half range
     h.build_device(_dev(v), _dev(t))  # a good build afterwards
