@@ -66,6 +66,8 @@ def lib():
         L.or_half_value.argtypes = [C.c_uint32]
         L.or_half_value.restype = D
         L.or_lattice_dv.argtypes = [P, I32, I32, P, P]
+        L.or_svb_encode.argtypes = [P, I32, P, P]
+        L.or_svb_encode.restype = I32
         L.or_tri_intersect.argtypes = [P, P, P]
         L.or_tri_intersect.restype = I32
         L.or_tri_dist.argtypes = [P, P]
@@ -284,6 +286,19 @@ def seg_seg(a, b, c, d) -> float:
 
 # quant_bits value of the half-precision descriptor mode
 QUANT_FP16 = 1
+# quant_bits value of the Stream VByte mode: exact lattice deltas to the parent, 1-4 bytes each
+QUANT_SVB = 2
+
+
+def svb_encode(values) -> tuple[bytes, bytes]:
+    """Stream VByte coding of up to 32 unsigned 32-bit values: (8-byte control word, data)."""
+    v = np.ascontiguousarray(values, dtype=np.uint32)
+    if len(v) > 32:
+        raise ValueError("at most 32 values per control word")
+    ctl = np.zeros(8, np.uint8)
+    data = np.zeros(4 * max(len(v), 1), np.uint8)
+    n = lib().or_svb_encode(_p(v), len(v), _p(ctl), _p(data))
+    return ctl.tobytes(), data[:n].tobytes()
 
 
 def half_rd(v: float) -> int:

@@ -17,6 +17,9 @@
  *     abstract and Sec. V), the corrector a small unsigned delta rounded outward.
  *   - treelets: the BVH clustered into parts of a byte budget (Sec. III-B), each root stored
  *     absolutely so every treelet is randomly accessible (abstract).
+ *   - the integer-compression alternative the conclusion proposes (quant_bits = 2): the
+ *     quantised bounds kept exact, each node's lattice interval stored as unsigned deltas to
+ *     its parent's, written in the Stream VByte format (Lemire, Kurz and Rupp 2018).
  *   - an independent decoder of the blob bytes.
  *   - simultaneous traversal, Algorithm 1 (BVHtraversal), recursive exactly as printed, with
  *     checkPrimitives = closed triangle-triangle intersection (CD) or triangle-triangle
@@ -180,6 +183,7 @@ typedef struct {
   int32_t **tlet_nodes;
   int lbits, max_tdepth;
   int rec_bytes, root_bytes;
+  int form_rec, form_root; /* record sizes the treelet formation assumes (see or_build) */
   int packing;  /* 0: treelets grown top-down; 1: packed bottom-up (see encode) */
   int headroom; /* lattice bits kept free: e is chosen for |bound| < 2^(30 - headroom) */
   uint8_t *blob;
@@ -352,8 +356,8 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   if (headroom < 0 || headroom > 8) return fail(OR_ERR_ARG, "headroom must be in [0, 8]");
   if (k != 6 && k != 18 && k != 24 && k != 26) return fail(OR_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (m != 2 && m != 4 && m != 8 && m != 16) return fail(OR_ERR_ARG, "branching must be 2, 4, 8 or 16");
-  if (bits != 0 && bits != 1 && bits != 8 && bits != 16)
-    return fail(OR_ERR_ARG, "quant_bits must be 0 (FP32), 1 (FP16), 8 or 16");
+  if (bits != 0 && bits != 1 && bits != 2 && bits != 8 && bits != 16)
+    return fail(OR_ERR_ARG, "quant_bits must be 0 (FP32), 1 (FP16), 2 (Stream VByte), 8 or 16");
   if (treelet_bytes < 4096 || treelet_bytes > 131072 || (treelet_bytes & (treelet_bytes - 1)))
     return fail(OR_ERR_ARG, "treelet_bytes must be a power of two in [4096, 131072]");
   if (nt < 1 || nt > 0x7fffffff || nv < 3 || nv > 0x7fffffff) return fail(OR_ERR_MESH, "bad mesh size");
@@ -370,7 +374,19 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
   h->root_bytes = 8 + 8 * h->K;
   h->rec_bytes = bits == 0 ? h->root_bytes : ((8 + h->K * 2 * (bits / 8) + 3) / 4) * 4;
   if (bits == 1) h->root_bytes = h->rec_bytes = 8 + 4 * h->K; /* absolute halves everywhere */
-  if (16 + h->root_bytes + m * h->rec_bytes > treelet_bytes) {
+  h->form_rec = h->rec_bytes;
+  h->form_root = h->root_bytes;
+  if (bits == 2) {
+    /* Stream VByte records have variable length: 8 B of topology, an 8-byte control word
+     * and 1 to 4 bytes per delta.  Treelets are formed with the largest record (16 + 8K B,
+     * the header's record size) plus its 2-byte entry in the treelet's offset table, and
+     * the root with its entry and the table's padding, so that every treelet stays within
+     * its budget whatever the deltas turn out to be. */
+    h->rec_bytes = 16 + 8 * h->K;
+    h->form_rec = h->rec_bytes + 2;
+    h->form_root = h->root_bytes + 4;
+  }
+  if (16 + h->form_root + m * h->form_rec > treelet_bytes) {
     or_free(h);
     return fail(OR_ERR_ARG, "treelet_bytes too small for one sibling group");
   }
@@ -572,6 +588,37 @@ static uint32_t f2u(float f) {
   return u;
 }
 
+/* Stream VByte (Lemire, Kurz and Rupp 2018): n unsigned 32-bit values as a 2-bit code per
+ * value (its byte count minus one; value i's code in bits 2i and 2i+1 of the control bytes,
+ * four codes per byte, little endian) followed by the values, little endian, each in the
+ * fewest of 1 to 4 bytes.  Here the control bytes are one 8-byte word (n <= 32).  Writes
+ * the control word to ctl8 and the value bytes to data; returns the number of data bytes. */
+static int svb_len(uint32_t v) { return v < (1u << 8) ? 1 : v < (1u << 16) ? 2 : v < (1u << 24) ? 3 : 4; }
+int or_svb_encode(const uint32_t *v, int n, uint8_t *ctl8, uint8_t *data) {
+  uint64_t ctl = 0;
+  int pos = 0;
+  for (int i = 0; i < n; ++i) {
+    const int len = svb_len(v[i]);
+    ctl |= (uint64_t)(len - 1) << (2 * i);
+    for (int b = 0; b < len; ++b) data[pos++] = (uint8_t)(v[i] >> (8 * b));
+  }
+  put64(ctl8, ctl);
+  return pos;
+}
+/* Bytes of a Stream VByte record: topology (8), control (8), the 2K deltas, padded to 4. */
+static int64_t svb_record_bytes(const or_bvh *h, int64_t x) {
+  int64_t n = 16;
+  for (int j = 0; j < 2 * h->K; ++j) n += svb_len(h->delta[x * h->K * 2 + j]);
+  return (n + 3) / 4 * 4;
+}
+/* Bytes of treelet t: header, offset table (Stream VByte only), records; before padding. */
+static int64_t treelet_bytes(const or_bvh *h, int64_t t) {
+  if (h->bits != 2) return 16 + h->root_bytes + (int64_t)(h->tlet_count[t] - 1) * h->rec_bytes;
+  int64_t sz = 16 + (2 * (int64_t)h->tlet_count[t] + 3) / 4 * 4 + h->root_bytes;
+  for (int32_t l = 1; l < h->tlet_count[t]; ++l) sz += svb_record_bytes(h, h->tlet_nodes[t][l]);
+  return sz;
+}
+
 /* Treelets packed bottom-up (Sec. III-B: treelets sized to the cache).  Going from the
  * deepest nodes up, each node carries the nodes of its subtree not yet cut off.  A node's
  * children stay in its treelet when the node plus everything its children carry still fits
@@ -581,7 +628,7 @@ static uint32_t f2u(float f) {
  * numbers); a treelet's nodes are listed breadth-first from its root. */
 static int pack_bottom_up(or_bvh *h) {
   int64_t nn = h->nn;
-  int64_t fit = (h->budget - 16 - h->root_bytes) / h->rec_bytes + 1; /* nodes per treelet */
+  int64_t fit = (h->budget - 16 - h->form_root) / h->form_rec + 1; /* nodes per treelet */
   int64_t *carry = (int64_t *)malloc(sizeof(int64_t) * nn);
   for (int64_t x = nn - 1; x >= 0; --x) {
     int64_t sum = 1;
@@ -663,7 +710,7 @@ static int encode(or_bvh *h) {
         h->tlet_nodes = (int32_t **)realloc(h->tlet_nodes, sizeof(int32_t *) * tcap);
       }
       int32_t r = h->tlet_root[t];
-      int64_t size = 16 + h->root_bytes;
+      int64_t size = 16 + h->form_root;
       int64_t cnt = 0, ncap = 64;
       int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * ncap);
       mem[cnt] = r;
@@ -675,8 +722,8 @@ static int encode(or_bvh *h) {
         int32_t x = bfs[bh++];
         int nc = h->nchild[x];
         if (nc == 0) continue;
-        if (size + (int64_t)nc * h->rec_bytes <= h->budget) {
-          size += (int64_t)nc * h->rec_bytes;
+        if (size + (int64_t)nc * h->form_rec <= h->budget) {
+          size += (int64_t)nc * h->form_rec;
           for (int c = 0; c < nc; ++c) {
             int32_t y = h->first[x] + c;
             if (cnt == ncap) {
@@ -731,6 +778,14 @@ static int encode(or_bvh *h) {
     int is_root = h->local[x] == 0;
     if (is_root || h->bits == 0 || h->bits == 1) {
       for (int j = 0; j < 2 * K; ++j) D[j] = C[j];
+    } else if (h->bits == 2) {
+      /* lossless: the deltas to the parent's interval, unshifted */
+      const int64_t *P = h->dec + (int64_t)h->parent[x] * K * 2;
+      for (int j = 0; j < K; ++j) {
+        h->delta[x * K * 2 + 2 * j] = (uint32_t)(C[2 * j] - P[2 * j]);
+        h->delta[x * K * 2 + 2 * j + 1] = (uint32_t)(P[2 * j + 1] - C[2 * j + 1]);
+      }
+      for (int j = 0; j < 2 * K; ++j) D[j] = C[j];
     } else {
       const int64_t *P = h->dec + (int64_t)h->parent[x] * K * 2;
       for (int j = 0; j < K; ++j) {
@@ -763,8 +818,7 @@ static int encode(or_bvh *h) {
   int64_t pos = off_t0;
   for (int64_t t = 0; t < h->ntlet; ++t) {
     toff[t] = pos;
-    int64_t sz = 16 + h->root_bytes + (int64_t)(h->tlet_count[t] - 1) * h->rec_bytes;
-    pos += (sz + 15) / 16 * 16;
+    pos += (treelet_bytes(h, t) + 15) / 16 * 16;
   }
   toff[h->ntlet] = pos;
   int64_t off_tris = pos;
@@ -803,9 +857,19 @@ static int encode(or_bvh *h) {
     put32(T, (uint32_t)h->tlet_count[t]);
     put32(T + 4, (uint32_t)first_node); /* blob-order index of the treelet's root */
     first_node += h->tlet_count[t];
+    /* Stream VByte: records of varying size, located by a table of 2-byte offsets (in
+     * 4-byte units from the treelet's start) after the header */
+    int64_t at = 16 + (2 * (int64_t)h->tlet_count[t] + 3) / 4 * 4;
     for (int32_t l = 0; l < h->tlet_count[t]; ++l) {
       int32_t x = h->tlet_nodes[t][l];
-      uint8_t *R = T + 16 + (l == 0 ? 0 : h->root_bytes + (int64_t)(l - 1) * h->rec_bytes);
+      uint8_t *R;
+      if (h->bits == 2) {
+        put16(T + 16 + 2 * l, (uint32_t)(at / 4));
+        R = T + at;
+        at += l == 0 ? h->root_bytes : svb_record_bytes(h, x);
+      } else {
+        R = T + 16 + (l == 0 ? 0 : h->root_bytes + (int64_t)(l - 1) * h->rec_bytes);
+      }
       int d = 0;
       for (int32_t y = x; h->local[y] != 0; y = h->parent[y]) ++d;
       uint32_t par = l == 0 ? 0xFFFFu : (uint32_t)h->local[h->parent[x]];
@@ -834,6 +898,8 @@ static int encode(or_bvh *h) {
             put32(R + 12 + 8 * j, (uint32_t)(int32_t)h->dec[x * K * 2 + 2 * j + 1]);
           }
         }
+      } else if (h->bits == 2) {
+        or_svb_encode(h->delta + x * K * 2, 2 * K, R + 8, R + 16);
       } else {
         for (int j = 0; j < K; ++j) {
           uint32_t dl = h->delta[x * K * 2 + 2 * j], dh = h->delta[x * K * 2 + 2 * j + 1];
@@ -956,7 +1022,20 @@ int64_t or_decode_blob(const uint8_t *blob, int64_t bytes, int32_t *lat, float *
       return fail(OR_ERR_ARG, "treelet header: wrong first-node index");
     }
     for (int32_t l = 0; l < cnt; ++l, ++n) {
-      const uint8_t *R = T + 16 + (l == 0 ? 0 : rootb + (int64_t)(l - 1) * rec);
+      const uint8_t *R = bits == 2 ? T + 4 * (int64_t)get16(T + 16 + 2 * l)
+                                   : T + 16 + (l == 0 ? 0 : rootb + (int64_t)(l - 1) * rec);
+      /* Stream VByte record: the 2K deltas from the control word's 2-bit length codes */
+      uint32_t sv[26];
+      if (bits == 2 && l > 0) {
+        const uint64_t ctl = get64(R + 8);
+        const uint8_t *q = R + 16;
+        for (int i = 0; i < 2 * K; ++i) {
+          const int len = (int)((ctl >> (2 * i)) & 3u) + 1;
+          sv[i] = 0;
+          for (int b = 0; b < len; ++b) sv[i] |= (uint32_t)q[b] << (8 * b);
+          q += len;
+        }
+      }
       uint32_t w0 = get32(R), w1 = get32(R + 4);
       int64_t *D = P + (int64_t)l * 2 * K;
       for (int j = 0; j < K; ++j) {
@@ -981,6 +1060,10 @@ int64_t or_decode_blob(const uint8_t *blob, int64_t bytes, int32_t *lat, float *
         if (l == 0) {
           D[2 * j] = (int32_t)get32(R + 8 + 8 * j);
           D[2 * j + 1] = (int32_t)get32(R + 12 + 8 * j);
+        } else if (bits == 2) {
+          const int64_t *Q = P + (int64_t)(w0 & 0xFFFFu) * 2 * K;
+          D[2 * j] = Q[2 * j] + (int64_t)sv[2 * j];
+          D[2 * j + 1] = Q[2 * j + 1] - (int64_t)sv[2 * j + 1];
         } else {
           const int64_t *Q = P + (int64_t)(w0 & 0xFFFFu) * 2 * K;
           int64_t lo = Q[2 * j], hi = Q[2 * j + 1];

@@ -11,6 +11,7 @@
 """
 import itertools
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -150,7 +151,8 @@ def test_tree_split_properties(m):
 @pytest.mark.parametrize("packing", [oracle.PACKING_TOP_DOWN, oracle.PACKING_BOTTOM_UP])
 @pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
                                          (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536),
-                                         (18, 4, 1, 4096), (24, 8, 1, 16384)])
+                                         (18, 4, 1, 4096), (24, 8, 1, 16384), (18, 4, 2, 4096), (24, 8, 2, 16384),
+                                         (26, 16, 2, 8192)])
 def test_encoding_invariants(k, m, bits, tb, packing):
     v, t = synth.icosphere(3, 1.0, 0.15, seed=5)
     h = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
@@ -165,6 +167,8 @@ def test_encoding_invariants(k, m, bits, tb, packing):
     # correctors fit b bits
     if bits >= 8:
         assert pl["delta"].max() <= (1 << bits) - 1
+    if bits == oracle.QUANT_SVB:  # lossless: the decoded intervals are the exact ones
+        assert (dec == ex).all()
     # the FP32 bounds contain the exact real bounds d.v of every vertex of the node
     e = h.e
     for x in range(0, h.n_nodes, 7):
@@ -174,11 +178,17 @@ def test_encoding_invariants(k, m, bits, tb, packing):
     roots = pl["local"] == 0
     assert (dec[roots] == ex[roots]).all()
     counts = np.bincount(pl["treelet"])
-    assert (16 + h.root_bytes + (counts - 1) * h.rec_bytes <= tb).all()
+    # (Stream VByte: formed with the largest record and its offset-table entry)
+    form_root, form_rec = (h.root_bytes + 4, h.rec_bytes + 2) if bits == oracle.QUANT_SVB else (h.root_bytes,
+                                                                                               h.rec_bytes)
+    assert (16 + form_root + (counts - 1) * form_rec <= tb).all()
+    blob = h.blob()
+    toff = blob[64:64 + 8 * (h.n_treelets + 1)].view(np.uint64).astype(np.int64)
+    assert (np.diff(toff) <= tb).all()  # the bytes actually written, padding included
     # the independent decoder reproduces the encoder, node by node
-    lat, f, meta = oracle.decode_blob(h.blob())
+    lat, f, meta = oracle.decode_blob(blob)
     order = np.lexsort((pl["local"], pl["treelet"]))
-    if bits >= 8:
+    if bits >= 8 or bits == oracle.QUANT_SVB:
         assert (lat == dec[order]).all()
     assert (f.view(np.uint32) == decf[order].view(np.uint32)).all()
     assert ((meta[:, 0] >> 16) & 31 == tr["nchild"][order]).all()
@@ -187,7 +197,7 @@ def test_encoding_invariants(k, m, bits, tb, packing):
     par_all = tr["parent"]
     nonroot = ~roots
     assert (pl["treelet"][nonroot] == pl["treelet"][par_all[nonroot]]).all()
-    fit = (tb - 16 - h.root_bytes) // h.rec_bytes + 1
+    fit = (tb - 16 - form_root) // form_rec + 1
     if packing == oracle.PACKING_BOTTOM_UP:
         # bottom-up rule, checked against its statement: an inner node's children were cut
         # off exactly when the node plus the nodes of their treelets would not fit one treelet
@@ -203,6 +213,58 @@ def test_encoding_invariants(k, m, bits, tb, packing):
         # treelets are numbered in node order of their roots
         rn = np.flatnonzero(roots)
         assert (pl["treelet"][rn] == np.arange(len(rn))).all()
+
+
+def _golden_svb():
+    path = os.path.join(os.path.dirname(__file__), "golden", "stream_vbyte.txt")
+    cases = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        vals, ctl, data = (x.split() for x in line.split("|"))
+        cases.append(([int(v, 0) for v in vals], bytes.fromhex("".join(ctl)), bytes.fromhex("".join(data))))
+    return cases
+
+
+@pytest.mark.parametrize("vals,ctl,data", _golden_svb())
+def test_stream_vbyte_format(vals, ctl, data):
+    """The Stream VByte coder of quant_bits = 2 against byte strings worked out by hand from
+    the format's published definition (Lemire, Kurz and Rupp 2018)."""
+    got_ctl, got_data = oracle.svb_encode(vals)
+    assert got_data == data
+    assert got_ctl[:len(ctl)] == ctl and got_ctl[len(ctl):] == bytes(8 - len(ctl))
+
+
+def test_stream_vbyte_records_hold_the_parent_deltas():
+    """A Stream VByte record's deltas are exactly C_lo - P_lo and P_hi - C_hi against the
+    parent's exact interval, read back from the blob bytes by the format's rule; and the
+    footprint lies between the 8-bit and the FP32 encodings of the same tree."""
+    v, t = synth.icosphere(3, 1.0, 0.15, seed=5)
+    h = oracle.BVH(v, t, 18, 4, oracle.QUANT_SVB, 4096)
+    tr, pl, ex = h.tree(), h.placement(), h.lattice()["exact"]
+    blob = h.blob()
+    toff = blob[64:64 + 8 * (h.n_treelets + 1)].view(np.uint64).astype(np.int64)
+    K = h.K
+    for x in range(1, h.n_nodes, 5):
+        if pl["local"][x] == 0:
+            continue
+        T = toff[pl["treelet"][x]]
+        off = 4 * int(blob[T + 16 + 2 * pl["local"][x]:T + 18 + 2 * pl["local"][x]].view(np.uint16)[0])
+        R = T + off
+        ctl = int.from_bytes(blob[R + 8:R + 16].tobytes(), "little")
+        q = R + 16
+        vals = []
+        for i in range(2 * K):
+            n = ((ctl >> (2 * i)) & 3) + 1
+            vals.append(int.from_bytes(blob[q:q + n].tobytes(), "little"))
+            q += n
+        p = tr["parent"][x]
+        want = [(ex[x, j, 0] - ex[p, j, 0], ex[p, j, 1] - ex[x, j, 1])[s] for j in range(K) for s in (0, 1)]
+        assert vals == want
+    b8 = oracle.BVH(v, t, 18, 4, 8, 4096).blob_bytes
+    b32 = oracle.BVH(v, t, 18, 4, 0, 4096).blob_bytes
+    assert b8 < h.blob_bytes < b32
 
 
 def test_half_precision_rounding_is_outward_and_tight():
