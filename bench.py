@@ -358,9 +358,10 @@ def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 100
 def compression(cb, torch, dev, c, steps=3):
     """The terrain step (CD with sorted pair lists + PQ, every pose) for each way of storing
     the bounds: 8- and 16-bit predictor-corrector deltas, FP16 descriptors (the paper's
-    measured mode, Sec. III-A) and uncompressed FP32.  Same hierarchy shape (24-DOP,
-    branching 8, 16 KB treelets); L2 flushed before every step; kernel time from the
-    library's events."""
+    measured mode, Sec. III-A), uncompressed FP32, and the integer compression the
+    conclusion proposes (exact lattice deltas in Stream VByte).  Same hierarchy shape
+    (24-DOP, branching 8, 16 KB treelets); L2 flushed before every step; kernel time from
+    the library's events; BV-pair tests of the collision query from the device counters."""
     import ctypes as C
     L = cb.lib
     sp = cb._stream_ptr(None)
@@ -368,7 +369,7 @@ def compression(cb, torch, dev, c, steps=3):
     P = torch.as_tensor(c["poses"], device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     out = []
-    for bits in (8, 16, 1, 0):
+    for bits in (8, 16, 1, 0, 2):
         A = cb.BVH(*c["A"], K_DOP, BRANCH, bits, TREELET, device=dev)
         B = cb.BVH(*c["B"], K_DOP, BRANCH, bits, TREELET, device=dev)
         cap = 16_000_000
@@ -407,8 +408,10 @@ def compression(cb, torch, dev, c, steps=3):
             pr = cb.profile_collect()
             ms["collide"] += pr["collide"][0] / steps
             ms["distance"] += pr["distance"][0] / steps
-        out.append({"mode": {8: "8-bit deltas", 16: "16-bit deltas", 1: "FP16", 0: "FP32"}[bits],
-                    "quant_bits": bits, "node_bytes": A.info["node_bytes"], "cd_ms": ms["collide"],
+        bv_cd = int(cb.query_stats(ws_c)[0])
+        out.append({"mode": {8: "8-bit deltas", 16: "16-bit deltas", 1: "FP16", 0: "FP32",
+                             2: "Stream VByte exact deltas"}[bits],
+                    "quant_bits": bits, "node_bytes": A.info["node_bytes"], "cd_bv_tests": bv_cd, "cd_ms": ms["collide"],
                     "pq_ms": ms["distance"], "pose_queries_per_s": 2 * n / ((ms["collide"] + ms["distance"]) / 1e3)})
         del A, B
         torch.cuda.empty_cache()

@@ -43,6 +43,7 @@ extern "C" {
 
 /* collide flags */
 #define CBVH_QUANT_FP16 1 /* quant_bits value of the half-precision descriptor mode */
+#define CBVH_QUANT_SVB 2  /* quant_bits value of the Stream VByte mode (exact deltas, 1-4 bytes) */
 #define CBVH_EARLY_EXIT 1u /* stop each pose at its first intersecting pair (pair outputs must be NULL);
                             * implied whenever no pair outputs are requested */
 #define CBVH_SORT_PAIRS 2u /* sort each pose's pair list by (i, j) */

@@ -380,11 +380,12 @@ int or_build(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, in
     /* Stream VByte records have variable length: 8 B of topology, an 8-byte control word
      * and 1 to 4 bytes per delta.  Treelets are formed with the largest record (16 + 8K B,
      * the header's record size) plus its 2-byte entry in the treelet's offset table, and
-     * the root with its entry and the table's padding, so that every treelet stays within
-     * its budget whatever the deltas turn out to be. */
+     * the root with its entry and the table's padding to 8 bytes (the absolute root record
+     * is 8-byte aligned), so that every treelet stays within its budget whatever the deltas
+     * turn out to be. */
     h->rec_bytes = 16 + 8 * h->K;
     h->form_rec = h->rec_bytes + 2;
-    h->form_root = h->root_bytes + 4;
+    h->form_root = h->root_bytes + 8;
   }
   if (16 + h->form_root + m * h->form_rec > treelet_bytes) {
     or_free(h);
@@ -614,7 +615,7 @@ static int64_t svb_record_bytes(const or_bvh *h, int64_t x) {
 /* Bytes of treelet t: header, offset table (Stream VByte only), records; before padding. */
 static int64_t treelet_bytes(const or_bvh *h, int64_t t) {
   if (h->bits != 2) return 16 + h->root_bytes + (int64_t)(h->tlet_count[t] - 1) * h->rec_bytes;
-  int64_t sz = 16 + (2 * (int64_t)h->tlet_count[t] + 3) / 4 * 4 + h->root_bytes;
+  int64_t sz = 16 + (2 * (int64_t)h->tlet_count[t] + 7) / 8 * 8 + h->root_bytes;
   for (int32_t l = 1; l < h->tlet_count[t]; ++l) sz += svb_record_bytes(h, h->tlet_nodes[t][l]);
   return sz;
 }
@@ -858,8 +859,8 @@ static int encode(or_bvh *h) {
     put32(T + 4, (uint32_t)first_node); /* blob-order index of the treelet's root */
     first_node += h->tlet_count[t];
     /* Stream VByte: records of varying size, located by a table of 2-byte offsets (in
-     * 4-byte units from the treelet's start) after the header */
-    int64_t at = 16 + (2 * (int64_t)h->tlet_count[t] + 3) / 4 * 4;
+     * 4-byte units from the treelet's start) after the header, padded to 8 bytes */
+    int64_t at = 16 + (2 * (int64_t)h->tlet_count[t] + 7) / 8 * 8;
     for (int32_t l = 0; l < h->tlet_count[t]; ++l) {
       int32_t x = h->tlet_nodes[t][l];
       uint8_t *R;

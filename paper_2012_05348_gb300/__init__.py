@@ -259,6 +259,8 @@ OPT_BUDGET0 = 3
 OPT_TREELET_PACKING = 4
 OPT_LATTICE_HEADROOM = 5
 PACK_TOP_DOWN, PACK_BOTTOM_UP = 0, 1
+# quant_bits values besides the delta widths 8 and 16
+QUANT_FP32, QUANT_FP16, QUANT_SVB = 0, 1, 2
 # CBVH_OPT_SPLIT values: warp per pose, rounds, work queue, rounds then work queue, and the
 # default (work queue for collision with pair lists, rounds then work queue otherwise)
 SPLIT_POSE, SPLIT_ROUNDS, SPLIT_QUEUE, SPLIT_ROUNDS_QUEUE, SPLIT_AUTO = 0, 1, 2, 3, 4

@@ -29,7 +29,11 @@
 //         int32 lattice values at a treelet root, b-bit correctors elsewhere, or FP32
 //         values (lo rounded down, hi rounded up) everywhere when quant_bits = 0, or FP16
 //         values rounded the same way (Sec. III-A's half-float descriptors) everywhere when
-//         quant_bits = 1.
+//         quant_bits = 1, or (quant_bits = 2) an 8-byte Stream VByte control word and the
+//         2K exact deltas to the parent's interval in 1 to 4 bytes each; such records vary in
+//         size (padded to 4 bytes) and are found through a table of 2-byte offsets, in
+//         4-byte units from the treelet's start, that follows the treelet header (padded
+//         to 8 bytes, so that the absolute root record is 8-byte aligned).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -240,6 +244,12 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
   const int k = h->k, K = h->K, branching = h->m, quant_bits = h->bits, treelet_bytes = h->treelet_bytes;
   const int64_t nn = (int64_t)nodes.size();
   for (const Node &nd : nodes) h->depth = std::max(h->depth, nd.depth);
+  // record sizes the treelet formation assumes: Stream VByte records vary, so treelets are
+  // formed with the largest record plus its offset-table entry (and the root with its entry
+  // and the table's padding to 8 bytes, which keeps the absolute root record 8-byte
+  // aligned), which keeps every treelet within its budget
+  const bool svb = quant_bits == CBVH_QUANT_SVB;
+  const int64_t form_root = h->root_bytes + (svb ? 8 : 0), form_rec = h->rec_bytes + (svb ? 2 : 0);
   // ---- treelets ----
   std::vector<int32_t> tlet(nn), local(nn), child_tlet(nn, -1);
   std::vector<uint8_t> ext(nn, 0);
@@ -250,7 +260,7 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
     // Bottom-up: `carry` counts the nodes of a subtree not yet cut off.  A node keeps its
     // children while it and everything they carry fit one treelet; else every child roots
     // a treelet of its own.  Treelets are numbered in node (BFS) order of their roots.
-    const int64_t fit = (treelet_bytes - 16 - h->root_bytes) / h->rec_bytes + 1;
+    const int64_t fit = (treelet_bytes - 16 - form_root) / form_rec + 1;
     std::vector<int64_t> carry(nn, 1);
     for (int64_t x = nn - 1; x >= 0; --x) {
       const Node &nd = nodes[x];
@@ -291,11 +301,11 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
       std::vector<int32_t> mem{roots[t]};
       tlet[roots[t]] = (int32_t)t;
       local[roots[t]] = 0;
-      int64_t used_bytes = 16 + h->root_bytes;
+      int64_t used_bytes = 16 + form_root;
       for (size_t i = 0; i < mem.size(); ++i) {  // `mem` doubles as the BFS queue
         const Node &nd = nodes[mem[i]];
         if (nd.count == 0) continue;
-        int64_t need = (int64_t)nd.count * h->rec_bytes;
+        int64_t need = (int64_t)nd.count * form_rec;
         if (used_bytes + need <= treelet_bytes) {
           used_bytes += need;
           for (int c = 0; c < nd.count; ++c) {
@@ -326,11 +336,21 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
   // ---- predictor-corrector encoding, top-down (parents precede children in BFS) ----
   std::vector<int32_t> dec((size_t)nn * K * 2);
   std::vector<uint16_t> corr((size_t)nn * K * 2, 0);
-  const uint32_t dmax = quant_bits ? (1u << quant_bits) - 1 : 0;
+  std::vector<uint32_t> sv(svb ? (size_t)nn * K * 2 : 0, 0);  // Stream VByte: exact deltas
+  const uint32_t dmax = quant_bits >= 8 ? (1u << quant_bits) - 1 : 0;
   for (int64_t x = 0; x < nn; ++x) {
     const int32_t *C = &lat[(size_t)x * K * 2];
     int32_t *D = &dec[(size_t)x * K * 2];
     if (local[x] == 0 || quant_bits == 0 || quant_bits == CBVH_QUANT_FP16) {
+      std::copy(C, C + 2 * K, D);
+      continue;
+    }
+    if (svb) {  // lossless: the unshifted deltas to the parent's exact interval
+      const int32_t *P = &lat[(size_t)nodes[x].parent * K * 2];
+      for (int j = 0; j < K; ++j) {
+        sv[(size_t)x * K * 2 + 2 * j] = (uint32_t)((int64_t)C[2 * j] - P[2 * j]);
+        sv[(size_t)x * K * 2 + 2 * j + 1] = (uint32_t)((int64_t)P[2 * j + 1] - C[2 * j + 1]);
+      }
       std::copy(C, C + 2 * K, D);
       continue;
     }
@@ -352,9 +372,20 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
   std::vector<int64_t> toff(ntl + 1);
   int64_t pos = (64 + 8 * (ntl + 1) + 15) / 16 * 16;
   h->off_treelets = pos;
+  auto svb_len = [](uint32_t v) { return v < (1u << 8) ? 1 : v < (1u << 16) ? 2 : v < (1u << 24) ? 3 : 4; };
+  auto rec_size = [&](int64_t x, bool root) -> int64_t {  // bytes of x's record
+    if (root) return h->root_bytes;
+    if (!svb) return h->rec_bytes;
+    int64_t n = 16;
+    for (int i = 0; i < 2 * K; ++i) n += svb_len(sv[(size_t)x * K * 2 + i]);
+    return (n + 3) / 4 * 4;
+  };
+  auto table_bytes = [&](int64_t count) -> int64_t { return svb ? (2 * count + 7) / 8 * 8 : 0; };
   for (int64_t t = 0; t < ntl; ++t) {
     toff[t] = pos;
-    pos += (16 + h->root_bytes + (int64_t)(members[t].size() - 1) * h->rec_bytes + 15) / 16 * 16;
+    int64_t sz = 16 + table_bytes((int64_t)members[t].size());
+    for (size_t l = 0; l < members[t].size(); ++l) sz += rec_size(members[t][l], l == 0);
+    pos += (sz + 15) / 16 * 16;
   }
   toff[ntl] = pos;
   h->off_tris = pos;
@@ -377,12 +408,15 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
     w32(b, T0 + 4, (uint32_t)first_node);
     first_node += (int64_t)mem.size();
     std::vector<int> tdepth(mem.size(), 0);
+    int64_t at = 16 + table_bytes((int64_t)mem.size());  // next record, from the treelet start
     for (size_t l = 0; l < mem.size(); ++l) {
       const int32_t x = mem[l];
       const Node &nd = nodes[x];
       if (l) tdepth[l] = tdepth[local[nd.parent]] + 1;
       max_td = std::max(max_td, tdepth[l]);
-      const int64_t R = T0 + 16 + (l ? h->root_bytes + (int64_t)(l - 1) * h->rec_bytes : 0);
+      const int64_t R = T0 + at;
+      if (svb) w16(b, T0 + 16 + 2 * (int64_t)l, (uint16_t)(at / 4));
+      at += rec_size(x, l == 0);
       uint32_t w0 = (l ? (uint32_t)local[nd.parent] : 0xFFFFu) | ((uint32_t)nd.count << 16) |
                     ((uint32_t)ext[x] << 21) | ((uint32_t)tdepth[l] << 24);
       uint32_t w1 = nd.count == 0 ? (uint32_t)leaf_slot[x]
@@ -390,6 +424,18 @@ int layout(cbvh_bvh *h, const std::vector<Node> &nodes, const std::vector<int32_
       w32(b, R, w0);
       w32(b, R + 4, w1);
       const int32_t *D = &dec[(size_t)x * K * 2];
+      if (svb && l) {  // Stream VByte: control word, then each delta in its fewest bytes
+        uint64_t ctl = 0;
+        int64_t q = R + 16;
+        for (int i = 0; i < 2 * K; ++i) {
+          const uint32_t v = sv[(size_t)x * K * 2 + i];
+          const int len = svb_len(v);
+          ctl |= (uint64_t)(len - 1) << (2 * i);
+          for (int y = 0; y < len; ++y) b[q++] = (uint8_t)(v >> (8 * y));
+        }
+        w64(b, R + 8, ctl);
+        continue;
+      }
       for (int j = 0; j < K; ++j) {
         if (quant_bits == 0) {
           w32(b, R + 8 + 8 * j, f32_bits(to_f32_down(D[2 * j], h->e)));
@@ -455,8 +501,9 @@ int new_handle(int64_t n_verts, int64_t n_tris, int k, int branching, int quant_
   if (k != 6 && k != 18 && k != 24 && k != 26) return cbvh::fail(CBVH_ERR_ARG, "k must be 6, 18, 24 or 26");
   if (branching != 2 && branching != 4 && branching != 8 && branching != 16)
     return cbvh::fail(CBVH_ERR_ARG, "branching must be 2, 4, 8 or 16");
-  if (quant_bits != 0 && quant_bits != CBVH_QUANT_FP16 && quant_bits != 8 && quant_bits != 16)
-    return cbvh::fail(CBVH_ERR_ARG, "quant_bits must be 0 (FP32), 1 (FP16), 8 or 16");
+  if (quant_bits != 0 && quant_bits != CBVH_QUANT_FP16 && quant_bits != CBVH_QUANT_SVB && quant_bits != 8 &&
+      quant_bits != 16)
+    return cbvh::fail(CBVH_ERR_ARG, "quant_bits must be 0 (FP32), 1 (FP16), 2 (Stream VByte), 8 or 16");
   if (treelet_bytes < 4096 || treelet_bytes > 131072 || (treelet_bytes & (treelet_bytes - 1)))
     return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes must be a power of two in [4096, 131072]");
   if (n_tris < 1 || n_tris > 0x7fffffff || n_verts < 3 || n_verts > 0x7fffffff)
@@ -471,11 +518,15 @@ int new_handle(int64_t n_verts, int64_t n_tris, int k, int branching, int quant_
   h->treelet_bytes = treelet_bytes;
   if (quant_bits == CBVH_QUANT_FP16) {  // absolute half-precision bounds in every record
     h->root_bytes = h->rec_bytes = 8 + 4 * K;
+  } else if (quant_bits == CBVH_QUANT_SVB) {  // absolute root; records of at most 16 + 8K bytes
+    h->root_bytes = 8 + 8 * K;
+    h->rec_bytes = 16 + 8 * K;
   } else {
     h->root_bytes = 8 + 8 * K;
     h->rec_bytes = quant_bits == 0 ? h->root_bytes : (8 + 2 * K * (quant_bits / 8) + 3) / 4 * 4;
   }
-  if (16 + h->root_bytes + branching * h->rec_bytes > treelet_bytes) {
+  const int svb_extra = quant_bits == CBVH_QUANT_SVB ? 8 + 2 * branching : 0;  // offset-table entries
+  if (16 + h->root_bytes + branching * h->rec_bytes + svb_extra > treelet_bytes) {
     delete h;
     return cbvh::fail(CBVH_ERR_ARG, "treelet_bytes too small for one sibling group");
   }
@@ -623,6 +674,8 @@ extern "C" int cbvh_build_plan(int64_t n_verts, int64_t n_tris, int k, int branc
   cbvh::clear_error();
   if (!out) return cbvh::fail(CBVH_ERR_ARG, "out is NULL");
   *out = nullptr;
+  if (quant_bits == CBVH_QUANT_SVB)
+    return cbvh::fail(CBVH_ERR_ARG, "the device build needs fixed-size records (quant_bits 0, 1, 8 or 16)");
   cbvh_bvh *h = nullptr;
   if (int rc = new_handle(n_verts, n_tris, k, branching, quant_bits, treelet_bytes, &h)) return rc;
   // the tree's shape depends on n_tris and the branching alone: split nothing, keep positions

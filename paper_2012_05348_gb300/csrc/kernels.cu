@@ -134,13 +134,36 @@ struct Params {
 __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
 
 __device__ __forceinline__ const uint8_t *treelet_base(const BVd &X, uint32_t t) { return X.blob + X.toff[t]; }
+// Record of local node l in the treelet at tb: fixed-size records follow the root, Stream
+// VByte records are found through the treelet's table of 2-byte offsets (4-byte units).
 __device__ __forceinline__ const uint8_t *rec_at(const BVd &X, const uint8_t *tb, uint32_t l) {
+  if (X.bits == CBVH_QUANT_SVB) return tb + 4u * (uint32_t)*reinterpret_cast<const uint16_t *>(tb + 16 + 2 * l);
   return tb + 16 + (l ? X.root + (int)(l - 1) * X.rec : 0);
 }
 __device__ __forceinline__ uint32_t ld32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+// Delta i of a Stream VByte record (Lemire, Kurz and Rupp 2018): its 2-bit code in the
+// control word gives its length (1 to 4 bytes); its offset is i plus the codes before it,
+// counted by two popcounts; the bytes are read from the one or two aligned words they span.
+__device__ __forceinline__ uint32_t svb_value(const uint8_t *r, unsigned long long ctl, int i) {
+  const unsigned long long below = ctl & ((1ull << (2 * i)) - 1ull);
+  const int off = 16 + i + __popcll(below & 0x5555555555555555ull) + 2 * __popcll(below & 0xaaaaaaaaaaaaaaaaull);
+  const int len = (int)((ctl >> (2 * i)) & 3ull) + 1;
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(r + (off & ~3));
+  const int sh = 8 * (off & 3);
+  const uint32_t v = (off & 3) + len > 4 ? __funnelshift_r(w[0], w[1], sh) : w[0] >> sh;
+  return len == 4 ? v : v & ((1u << (8 * len)) - 1u);
+}
+// Stream VByte corrector of direction j: the exact deltas to the parent's interval.
+__device__ __forceinline__ int2 svb_delta(int2 P, const uint8_t *r, int j) {
+  const unsigned long long ctl = (unsigned long long)ld32(r + 8) | ((unsigned long long)ld32(r + 12) << 32);
+  const uint32_t dl = svb_value(r, ctl, 2 * j), dh = svb_value(r, ctl, 2 * j + 1);
+  return make_int2((int)((uint32_t)P.x + dl), (int)((uint32_t)P.y - dh));
+}
+
 // Corrector of direction j in a non-root record.
 __device__ __forceinline__ int2 apply_delta(int2 P, const uint8_t *r, int bits, int j) {
+  if (bits == CBVH_QUANT_SVB) return svb_delta(P, r, j);
   uint32_t dl, dh;
   if (bits == 8) {
     uint32_t v = *reinterpret_cast<const uint16_t *>(r + 8 + 2 * j);
@@ -162,6 +185,7 @@ __device__ __forceinline__ int delta_shift(int2 P, int bits) {
 }
 // apply_delta with the shift already known (it depends on the parent only).
 __device__ __forceinline__ int2 apply_delta_s(int2 P, const uint8_t *r, int bits, int j, int s) {
+  if (bits == CBVH_QUANT_SVB) return svb_delta(P, r, j);
   uint32_t dl, dh;
   if (bits == 8) {
     const uint32_t v = *reinterpret_cast<const uint16_t *>(r + 8 + 2 * j);

@@ -276,6 +276,8 @@ extern "C" int cbvh_refit_workspace_bytes(const cbvh_bvh *h, int64_t *bytes) {
 extern "C" int cbvh_refit_prepare(cbvh_bvh *h, void *workspace, int64_t workspace_bytes, void *stream) {
   cbvh::clear_error();
   if (!h || !workspace) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  if (h->bits == CBVH_QUANT_SVB)  // a record's size follows its deltas: no re-encoding in place
+    return cbvh::fail(CBVH_ERR_ARG, "refit needs fixed-size records (quant_bits 0, 1, 8 or 16)");
   const RefitLayout L = refit_layout(h);
   if (workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return cbvh::fail(CBVH_ERR_WORKSPACE, "refit workspace too small or not 256-byte aligned");

@@ -37,7 +37,8 @@ def test_library_exports_every_declared_symbol(cb):
 
 
 CONFIGS = [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096), (26, 16, 16, 8192), (18, 4, 0, 4096),
-           (24, 8, 16, 65536), (18, 2, 16, 131072), (18, 16, 8, 32768), (18, 4, 1, 4096), (26, 8, 1, 16384)]
+           (24, 8, 16, 65536), (18, 2, 16, 131072), (18, 16, 8, 32768), (18, 4, 1, 4096), (26, 8, 1, 16384),
+           (18, 4, 2, 4096), (24, 8, 2, 16384), (26, 16, 2, 8192), (6, 2, 2, 131072)]
 
 
 @pytest.fixture(params=[0, 1], ids=["top_down", "bottom_up"])

@@ -62,7 +62,8 @@ def bottom_up(cb):
 @pytest.mark.parametrize("packing", [0, 1])
 @pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096),
                                          (26, 16, 16, 8192), (18, 4, 0, 4096), (24, 8, 16, 65536),
-                                         (18, 4, 1, 4096), (24, 8, 1, 16384)])
+                                         (18, 4, 1, 4096), (24, 8, 1, 16384), (18, 4, 2, 4096), (24, 8, 2, 16384),
+                                         (26, 16, 2, 8192), (6, 2, 2, 65536)])
 def test_decode_bit_exact(cb, k, m, bits, tb, packing):
     v, t = synth.icosphere(4, 1.0, 0.15, seed=40 + k)
     cb.set_option(cb.OPT_TREELET_PACKING, packing)
@@ -73,13 +74,14 @@ def test_decode_bit_exact(cb, k, m, bits, tb, packing):
     lat, f = h.decode_all()
     o_lat, o_f, _ = oracle.decode_blob(h.blob_host())
     assert (f.cpu().numpy().view(np.uint32) == o_f.view(np.uint32)).all()
-    if bits >= 8:
+    if bits >= 8 or bits == 2:
         assert (lat.cpu().numpy() == o_lat).all()
 
 
-def test_decode_bit_exact_terrain(cb):
+@pytest.mark.parametrize("bits", [8, 2])
+def test_decode_bit_exact_terrain(cb, bits):
     c = synth.C2(1, cells=512)
-    h = cb.BVH(*c["A"], 24, 8, 8, 16384)
+    h = cb.BVH(*c["A"], 24, 8, bits, 16384)
     lat, f = h.decode_all()
     o_lat, o_f, _ = oracle.decode_blob(h.blob_host())
     assert (lat.cpu().numpy() == o_lat).all()
@@ -138,7 +140,8 @@ def test_brute_force_agrees_on_a_c1_subset(cb, c1):
 
 @pytest.mark.parametrize("k,m,bits,tb", [(6, 2, 8, 4096), (18, 4, 0, 4096), (18, 4, 8, 4096), (24, 8, 16, 16384),
                                          (26, 16, 16, 8192), (24, 16, 8, 131072), (18, 2, 16, 65536),
-                                         (18, 4, 1, 4096), (24, 8, 1, 16384)])
+                                         (18, 4, 1, 4096), (24, 8, 1, 16384), (18, 4, 2, 4096), (24, 8, 2, 16384),
+                                         (26, 16, 2, 8192)])
 def test_other_configs_bit_exact(cb, c1, k, m, bits, tb):
     va, ta, vb, tb_ = c1["mesh"]
     A = cb.BVH(va, ta, k, m, bits, tb)
@@ -151,7 +154,8 @@ def test_other_configs_bit_exact(cb, c1, k, m, bits, tb):
     assert np.abs(d - o_d).max() <= TOL_PQ * c1["D"]
 
 
-@pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (18, 4, 8, 131072), (18, 4, 0, 16384)])
+@pytest.mark.parametrize("k,m,bits,tb", [(18, 4, 16, 4096), (24, 8, 8, 16384), (18, 4, 8, 131072), (18, 4, 0, 16384),
+                                         (24, 8, 2, 16384)])
 def test_bottom_up_packing_bit_exact(cb, c1, bottom_up, k, m, bits, tb):
     va, ta, vb, tb_ = c1["mesh"]
     A = cb.BVH(va, ta, k, m, bits, tb)

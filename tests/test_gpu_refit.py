@@ -117,3 +117,7 @@ def test_refit_reports_bad_vertices(cb):
         h16.refit(_dev(v * 45000.0), T)  # ... not after (the lattice itself has room)
     h.refit(_dev(v), T)  # a good refit afterwards restores the build's blob
     assert (h.blob_dev.cpu().numpy() == h.blob_host()).all()
+    hs = cb.BVH(v, t, 18, 4, 2, 4096)  # Stream VByte: record sizes follow the deltas
+    with pytest.raises(cb.CbvhError) as e:
+        hs.refit(_dev(v), T)
+    assert e.value.code == -1

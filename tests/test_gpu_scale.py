@@ -44,7 +44,8 @@ def field(cb):
     return dict(mesh=(va, ta, vb, tb), Ao=Ao, Bo=Bo, D=D, P=P)
 
 
-@pytest.mark.parametrize("bits,tb", [(8, 16384), (16, 16384), (0, 16384), (1, 16384), (8, 131072), (16, 65536)])
+@pytest.mark.parametrize("bits,tb", [(8, 16384), (16, 16384), (0, 16384), (1, 16384), (8, 131072), (16, 65536),
+                                     (2, 16384)])
 def test_reduced_field_against_oracle(cb, field, bits, tb):
     import torch
     va, ta, vb, tb_ = field["mesh"]

@@ -179,12 +179,18 @@ def test_encoding_invariants(k, m, bits, tb, packing):
     assert (dec[roots] == ex[roots]).all()
     counts = np.bincount(pl["treelet"])
     # (Stream VByte: formed with the largest record and its offset-table entry)
-    form_root, form_rec = (h.root_bytes + 4, h.rec_bytes + 2) if bits == oracle.QUANT_SVB else (h.root_bytes,
+    form_root, form_rec = (h.root_bytes + 8, h.rec_bytes + 2) if bits == oracle.QUANT_SVB else (h.root_bytes,
                                                                                                h.rec_bytes)
     assert (16 + form_root + (counts - 1) * form_rec <= tb).all()
     blob = h.blob()
     toff = blob[64:64 + 8 * (h.n_treelets + 1)].view(np.uint64).astype(np.int64)
     assert (np.diff(toff) <= tb).all()  # the bytes actually written, padding included
+    assert (toff % 16 == 0).all()
+    if bits == oracle.QUANT_SVB:  # every absolute root record 8-byte aligned, every record 4
+        for t in range(h.n_treelets):
+            c = int(blob[toff[t]:toff[t] + 4].view(np.uint32)[0])
+            offs = 4 * blob[toff[t] + 16:toff[t] + 16 + 2 * c].view(np.uint16).astype(np.int64)
+            assert offs[0] % 8 == 0 and offs[0] >= 16 + 2 * c and (np.diff(offs) > 0).all()
     # the independent decoder reproduces the encoder, node by node
     lat, f, meta = oracle.decode_blob(blob)
     order = np.lexsort((pl["local"], pl["treelet"]))

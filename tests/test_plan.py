@@ -98,6 +98,9 @@ def test_plan_argument_errors(cb):
         with pytest.raises(cb.CbvhError) as e:
             cb.BVH.plan(*args, device=None)
         assert e.value.code == -1
+    with pytest.raises(cb.CbvhError) as e:  # Stream VByte records: sizes follow the geometry
+        cb.BVH.plan(100, 50, 18, 4, 2, 4096, device=None)
+    assert e.value.code == -1
     for nv, nt in [(2, 10), (100, 0)]:
         with pytest.raises(cb.CbvhError) as e:
             cb.BVH.plan(nv, nt, 18, 4, 8, 4096, device=None)
