@@ -78,7 +78,13 @@ const char *cbvh_last_error(void);
  *      the parent's decoded interval, corrector = outward b-bit delta; CBVH_QUANT_FP16
  *      (1) -- absolute half-precision bounds, lo rounded down and hi rounded up (the
  *      half-float descriptors of Sec. III-A; bounds beyond +-65504 become infinite); 0 --
- *      uncompressed FP32 bounds.
+ *      uncompressed FP32 bounds; CBVH_QUANT_SVB (2) -- the integer compression the
+ *      conclusion proposes: exact lattice bounds, each node's interval stored as unsigned
+ *      deltas to its parent's in the Stream VByte format (Lemire, Kurz and Rupp 2018: a
+ *      2-bit length code per delta in an 8-byte control word, then 1 to 4 bytes per
+ *      delta), records of varying size found through a per-treelet offset table.  Stream
+ *      VByte hierarchies are not refitted, built on the device or batched
+ *      (CBVH_ERR_ARG).
  *   treelet_bytes: power of two in [4096, 131072]; the hierarchy is clustered into treelets
  *      of at most this size (Sec. III-B), each with an absolute root for random access.
  * On success *out receives a handle owning host memory only; attach a device copy of its

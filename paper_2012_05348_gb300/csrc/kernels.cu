@@ -136,8 +136,11 @@ __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st
 __device__ __forceinline__ const uint8_t *treelet_base(const BVd &X, uint32_t t) { return X.blob + X.toff[t]; }
 // Record of local node l in the treelet at tb: fixed-size records follow the root, Stream
 // VByte records are found through the treelet's table of 2-byte offsets (4-byte units).
+// VAR: the code may meet Stream VByte hierarchies (a separate compilation of the decode
+// path, so that the fixed-size modes carry none of it).
+template <bool VAR>
 __device__ __forceinline__ const uint8_t *rec_at(const BVd &X, const uint8_t *tb, uint32_t l) {
-  if (X.bits == CBVH_QUANT_SVB) return tb + 4u * (uint32_t)*reinterpret_cast<const uint16_t *>(tb + 16 + 2 * l);
+  if (VAR && X.bits == CBVH_QUANT_SVB) return tb + 4u * (uint32_t)*reinterpret_cast<const uint16_t *>(tb + 16 + 2 * l);
   return tb + 16 + (l ? X.root + (int)(l - 1) * X.rec : 0);
 }
 __device__ __forceinline__ uint32_t ld32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
@@ -162,8 +165,9 @@ __device__ __forceinline__ int2 svb_delta(int2 P, const uint8_t *r, int j) {
 }
 
 // Corrector of direction j in a non-root record.
+template <bool VAR>
 __device__ __forceinline__ int2 apply_delta(int2 P, const uint8_t *r, int bits, int j) {
-  if (bits == CBVH_QUANT_SVB) return svb_delta(P, r, j);
+  if (VAR && bits == CBVH_QUANT_SVB) return svb_delta(P, r, j);
   uint32_t dl, dh;
   if (bits == 8) {
     uint32_t v = *reinterpret_cast<const uint16_t *>(r + 8 + 2 * j);
@@ -184,8 +188,9 @@ __device__ __forceinline__ int delta_shift(int2 P, int bits) {
   return max(0, (32 - __clz((int)range)) - bits);
 }
 // apply_delta with the shift already known (it depends on the parent only).
+template <bool VAR>
 __device__ __forceinline__ int2 apply_delta_s(int2 P, const uint8_t *r, int bits, int j, int s) {
-  if (bits == CBVH_QUANT_SVB) return svb_delta(P, r, j);
+  if (VAR && bits == CBVH_QUANT_SVB) return svb_delta(P, r, j);
   uint32_t dl, dh;
   if (bits == 8) {
     const uint32_t v = *reinterpret_cast<const uint16_t *>(r + 8 + 2 * j);
@@ -244,6 +249,7 @@ __device__ __forceinline__ const uint8_t *tbase(const BVd &X, const Side &S, uin
 // refreshing the cache on the way.  Returns x's record; all lanes must call it.
 // w0: the first word of x's record (the caller has it); S.cur_t / cur_base must hold x's
 // treelet.
+template <bool VAR>
 __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, const uint8_t *rx, int lane,
                              int2 &P) {
   const uint32_t t = x >> X.lbits, l = x & X.lmask;
@@ -258,7 +264,7 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, con
   }
   if (d > 0 && S.tag[d - 1] == (tb | (w & 0xffffu))) {
     if (act) {
-      P = apply_delta(S.lat[(d - 1) * S.nd + lane], rx, X.bits, lane);
+      P = apply_delta<VAR>(S.lat[(d - 1) * S.nd + lane], rx, X.bits, lane);
       S.lat[d * S.nd + lane] = P;
     }
     if (lane == 0) S.tag[d] = tb | l;
@@ -279,12 +285,12 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, con
       start = dd;
       break;
     }
-    w = ld32(rec_at(X, S.cur_base, ll));  // not cached: its record leads one level up
+    w = ld32(rec_at<VAR>(X, S.cur_base, ll));  // not cached: its record leads one level up
   }
   __syncwarp();
   if (start < 0) {
     if (act) {
-      P = abs_lattice(rec_at(X, S.cur_base, 0), lane);
+      P = abs_lattice(rec_at<VAR>(X, S.cur_base, 0), lane);
       S.lat[lane] = P;
     }
     if (lane == 0) S.tag[0] = tb;
@@ -295,7 +301,7 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, con
   for (int lev = start + 1; lev <= d; ++lev) {
     const uint32_t pl = (uint32_t)S.path[lev];
     if (act) {
-      P = apply_delta(P, rec_at(X, S.cur_base, pl), X.bits, lane);
+      P = apply_delta<VAR>(P, rec_at<VAR>(X, S.cur_base, pl), X.bits, lane);
       S.lat[lev * S.nd + lane] = P;
     }
     if (lane == 0) S.tag[lev] = tb | pl;
@@ -308,7 +314,7 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, con
 // written to iv (row stride KS), references to ref[], and leaf slots (or 0xffffffff) to
 // leaf[].  Returns
 // the number of members (warp-uniform).
-template <int ND>
+template <int ND, bool VAR>
 __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float2 *iv, int KS,
                           uint32_t *ref, uint32_t *leaf, int *shift, bool leaf_bounds = true) {
   const uint32_t t = x >> X.lbits;
@@ -316,7 +322,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     S.cur_t = t;
     S.cur_base = tbase(X, S, t);
   }
-  const uint8_t *rx = rec_at(X, S.cur_base, x & X.lmask);
+  const uint8_t *rx = rec_at<VAR>(X, S.cur_base, x & X.lmask);
   const uint32_t w0 = ld32(rx), w1 = ld32(rx + 4);
   const int nc = (int)((w0 >> 16) & 31u);
   const bool ext = (w0 >> 21) & 1u;
@@ -344,10 +350,10 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
         uint32_t cref;
         if (ext) {
           cref = (w1 + i) << X.lbits;
-          rc = rec_at(X, tbase(X, S, w1 + i), 0);
+          rc = rec_at<VAR>(X, tbase(X, S, w1 + i), 0);
         } else {
           cref = (t << X.lbits) | (w1 + i);
-          rc = rec_at(X, S.cur_base, w1 + i);
+          rc = rec_at<VAR>(X, S.cur_base, w1 + i);
         }
         iv[i * KS + j] = abs_bound(rc, j, X.bits);
         if (j == 0) {
@@ -362,7 +368,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
   }
   int2 P = make_int2(0, 0);  // x's decoded interval (lanes < nd)
   if (self || !ext) {
-    chain_decode(X, S, x, w0, rx, lane, P);
+    chain_decode<VAR>(X, S, x, w0, rx, lane, P);
     if (self) {
       if (lane < nd) iv[lane] = lat_to_f(P, X.scale);
       if (lane == 0) {
@@ -383,12 +389,12 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     int2 L;
     if (ext) {
       cref = (w1 + i) << X.lbits;
-      rc = rec_at(X, tbase(X, S, w1 + i), 0);
+      rc = rec_at<VAR>(X, tbase(X, S, w1 + i), 0);
       L = abs_lattice(rc, j);
     } else {
       cref = (t << X.lbits) | (w1 + i);
-      rc = rec_at(X, S.cur_base, w1 + i);
-      L = apply_delta_s(S.lat[d * nd + j], rc, X.bits, j, shift[j]);
+      rc = rec_at<VAR>(X, S.cur_base, w1 + i);
+      L = apply_delta_s<VAR>(S.lat[d * nd + j], rc, X.bits, j, shift[j]);
     }
     iv[i * KS + j] = lat_to_f(L, X.scale);
     if (j == 0) {
@@ -717,7 +723,7 @@ __device__ __noinline__ int queue_take(const Params &p, unsigned int *qc, uint32
   return 0;
 }
 
-template <int MODE, int KA, bool BATCH>
+template <int MODE, int KA, bool BATCH, bool VAR>
 __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traverse_kernel(const Params p) {
   uint8_t *smem = g_dsmem;
   const int lane = threadIdx.x & 31;
@@ -994,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       // order one of them is often the same as in the previous expansion and is reused.
       int na, nb;
       if (a != keyA || root) {
-        na = decode_set<KA>(A, SA, a, root, lane, aiv, KS, aref, aleaf, shift);
+        na = decode_set<KA, VAR>(A, SA, a, root, lane, aiv, KS, aref, aleaf, shift);
         keyA = root ? 0xffffffffu : a;
         na_c = na;
         abox_ok = false;
@@ -1002,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         na = na_c;
       }
       if (b != keyB || root) {
-        nb = decode_set<3>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
+        nb = decode_set<3, VAR>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
         if (lane < nb && bleaf[lane] == 0xffffffffu) member_box(bvv, lane, bcm[lane], bhm[lane]);
         if (lane < 3 * nb) {  // leaf members: the exact box of their triangle
           const int i = lane / 3, x = lane - 3 * i;
@@ -1425,16 +1431,16 @@ __global__ void decode_all_kernel(const BVd X, int32_t *lat_out, float *f_out) {
   const uint32_t cnt = ld32(tb), first = ld32(tb + 4);
   for (uint32_t it = threadIdx.x; it < cnt * (uint32_t)X.K; it += blockDim.x) {
     const uint32_t l = it / X.K, j = it - l * X.K;
-    const uint8_t *r = rec_at(X, tb, l);
+    const uint8_t *r = rec_at<true>(X, tb, l);
     float2 f;
     if (X.bits <= 1) {
       f = abs_bound(r, j, X.bits);
     } else {
       uint32_t path[64];
       int d = 0;
-      for (uint32_t y = l; y != 0 && d < 64; y = ld32(rec_at(X, tb, y)) & 0xffffu) path[d++] = y;
-      int2 P = abs_lattice(rec_at(X, tb, 0), j);
-      for (int q = d - 1; q >= 0; --q) P = apply_delta(P, rec_at(X, tb, path[q]), X.bits, j);
+      for (uint32_t y = l; y != 0 && d < 64; y = ld32(rec_at<true>(X, tb, y)) & 0xffffu) path[d++] = y;
+      int2 P = abs_lattice(rec_at<true>(X, tb, 0), j);
+      for (int q = d - 1; q >= 0; --q) P = apply_delta<true>(P, rec_at<true>(X, tb, path[q]), X.bits, j);
       f = lat_to_f(P, X.scale);
       if (lat_out) {
         lat_out[((size_t)(first + l) * X.K + j) * 2] = P.x;
@@ -1631,18 +1637,20 @@ int device_sms(int *sms) {
 
 // The traversal kernel compiled for A's number of slab directions (k = 6, 18, 24, 26).
 typedef void (*TraverseFn)(const Params);
-template <int MODE, bool BATCH>
+// var: a Stream VByte hierarchy takes part (single queries only; batches refuse them).
+template <int MODE, bool BATCH, bool VAR>
 TraverseFn traverse_fn_b(int K) {
   switch (K) {
-    case 3: return traverse_kernel<MODE, 3, BATCH>;
-    case 9: return traverse_kernel<MODE, 9, BATCH>;
-    case 12: return traverse_kernel<MODE, 12, BATCH>;
-    default: return traverse_kernel<MODE, 13, BATCH>;
+    case 3: return traverse_kernel<MODE, 3, BATCH, VAR>;
+    case 9: return traverse_kernel<MODE, 9, BATCH, VAR>;
+    case 12: return traverse_kernel<MODE, 12, BATCH, VAR>;
+    default: return traverse_kernel<MODE, 13, BATCH, VAR>;
   }
 }
 template <int MODE>
-TraverseFn traverse_fn(int K, bool batch = false) {
-  return batch ? traverse_fn_b<MODE, true>(K) : traverse_fn_b<MODE, false>(K);
+TraverseFn traverse_fn(int K, bool batch = false, bool var = false) {
+  if (batch) return traverse_fn_b<MODE, true, false>(K);
+  return var ? traverse_fn_b<MODE, false, true>(K) : traverse_fn_b<MODE, false, false>(K);
 }
 
 // Launches one traversal pass.  ctr: 24 zeroed u32 counters -- [0, 8) the task cursor of
@@ -1666,7 +1674,8 @@ template <int MODE>
 int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint32_t *ready, uint2 *stacks,
                   uint32_t task_cap, int sms, cudaStream_t s, int slot = MODE, bool early_all = false) {
   const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
-  const TraverseFn fn = traverse_fn<MODE>(p.A.K, p.items != nullptr);
+  const TraverseFn fn =
+      traverse_fn<MODE>(p.A.K, p.items != nullptr, p.A.bits == CBVH_QUANT_SVB || p.B.bits == CBVH_QUANT_SVB);
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
@@ -2002,7 +2011,7 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
                       "this pair of hierarchies needs " + std::to_string(per_warp * kWarpsPerBlock + stacks_off) +
                           " bytes of scratch; cbvh_distance_noalloc has " + std::to_string(kNoAllocScratchBytes));
   const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
-  const TraverseFn fn = traverse_fn<MODE_PQ>(p.A.K, false);
+  const TraverseFn fn = traverse_fn<MODE_PQ>(p.A.K, false, p.A.bits == CBVH_QUANT_SVB || p.B.bits == CBVH_QUANT_SVB);
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
@@ -2073,6 +2082,8 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
   for (int64_t i = 0; i < nq; ++i) {
     const cbvh_query_t &x = q[i];
     if (int rc = check_pair(x.A, x.B)) return rc;
+    if (x.A->bits == CBVH_QUANT_SVB || x.B->bits == CBVH_QUANT_SVB)
+      return cbvh::fail(CBVH_ERR_ARG, "batches need fixed-size records (quant_bits 0, 1, 8 or 16)");
     if ((x.mode != 0 && x.mode != 1) || x.n < 0 || (x.n > 0 && !x.poses))
       return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": bad mode, size or poses");
     if (x.n > 0 && ((x.mode == 0 && !x.hit) || (x.mode == 1 && !x.dist)))
