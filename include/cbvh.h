@@ -279,7 +279,9 @@ int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, const int32
  *   cbvh_build_device_workspace_bytes: device bytes of the build's scratch (about 110 B per
  *     triangle, plus the refit plan of cbvh_refit_workspace_bytes at its front).
  *   cbvh_build_device: verts_dev n_verts x 3 FP32, tris_dev n_tris x 3 int32 (device
- *     pointers, the plan's counts); workspace 256-byte aligned, caller-owned.  Builds into
+ *     pointers, the plan's counts); workspace 256-byte aligned, caller-owned and kept
+ *     unchanged between builds (the node plan is uploaded into it by the first build with
+ *     that workspace, and again whenever another workspace is passed).  Builds into
  *     the attached blob on `stream` and synchronises it (the lattice exponent is read back
  *     once).  May be called again with new geometry of the same counts (a new frame); the
  *     workspace also serves cbvh_refit afterwards.  flags: CBVH_BUILD_HOST_COPY copies the
