@@ -13,7 +13,7 @@
 //      decided exactly (the candidates around ilogb of the rounded maximum are tested with
 //      the expansion arithmetic of the refit);
 //   3. three lists of the triangles, each sorted by (centroid key on one axis, index) --
-//      least-significant-digit radix sort, 4-bit digits, skipping digits no key varies in;
+//      least-significant-digit radix sort, 8-bit digits, skipping digits no key varies in;
 //   4. the median splits, one round per level of the binary split tree: every segment of
 //      two or more triangles picks its axis of largest centroid extent (the ends of that
 //      axis's list), keeps the first half of that list on the left, and the other two lists
@@ -38,6 +38,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256, kItems = 4, kTile = kThreads * kItems;
+constexpr int kDigitBits = 8, kDigits = 1 << kDigitBits;  // radix of the sort
 
 // mesh faults found on the device (bits of Scalars::flags)
 enum : uint32_t { F_INDEX = 1u, F_DEGENERATE = 2u, F_NONFINITE = 4u, F_EXTENT = 8u, F_RANGE = 16u };
@@ -80,8 +81,8 @@ BuildLayout build_layout(const cbvh_bvh *h) {
   B.L0 = take(12 * nt);
   B.L1 = take(12 * nt);
   B.X = take(12 * nt);
-  B.hist = take(4 * 16 * nblk);
-  B.sums = take(4 * std::max(tiles(3 * nt), tiles(16 * nblk)));
+  B.hist = take(4 * kDigits * nblk);
+  B.sums = take(4 * std::max(tiles(3 * nt), tiles(kDigits * nblk)));
   B.seg_s = take(4 * nt);
   B.seg_n = take(4 * nt);
   B.flag = take(nt);
@@ -326,9 +327,10 @@ __global__ void __launch_bounds__(1024) scan_sums(uint32_t *sums, int64_t nb) {
   }
 }
 
-__global__ void scan_add(uint32_t *out, int64_t n, const uint32_t *sums) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] += sums[i / kTile];
+// Value i of a scan done by scan_tiles + scan_sums: the tile's own prefix plus the tiles
+// before it (the consumers add it, saving a pass over the array).
+__device__ __forceinline__ uint32_t scanned(const uint32_t *X, const uint32_t *sums, int64_t i) {
+  return X[i] + sums[i / kTile];
 }
 
 template <class In>
@@ -336,8 +338,7 @@ void exclusive_scan(In in, uint32_t *out, int64_t n, uint32_t *sums, cudaStream_
   const int64_t nb = tiles(n);
   scan_tiles<In><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, sums);
   scan_sums<<<1, 1024, 0, s>>>(sums, nb);
-  scan_add<<<grid(n), 256, 0, s>>>(out, n, sums);
-  launches += 3;
+  launches += 2;
 }
 
 // ---------------------------------------------------------------- 3: radix sort (stable LSD)
@@ -349,16 +350,16 @@ __global__ void iota_kernel(int32_t *v, int64_t n) {
 // Digit counts of each tile, digit-major: hist[d * nblk + tile].
 __global__ void __launch_bounds__(kThreads) rs_hist(const unsigned long long *keys, int64_t n, int shift,
                                                    uint32_t *hist, int64_t nblk) {
-  __shared__ uint32_t cnt[16];
-  if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
+  __shared__ uint32_t cnt[kDigits];
+  for (int e = threadIdx.x; e < kDigits; e += kThreads) cnt[e] = 0;
   __syncthreads();
   const int64_t base = blockIdx.x * (int64_t)kTile;
   for (int q = 0; q < kItems; ++q) {
     const int64_t i = base + q * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 15u], 1u);
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & (kDigits - 1u)], 1u);
   }
   __syncthreads();
-  if (threadIdx.x < 16) hist[threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+  for (int e = threadIdx.x; e < kDigits; e += kThreads) hist[e * nblk + blockIdx.x] = cnt[e];
 }
 
 // Stable scatter by one digit: an element's destination is the scanned count of smaller
@@ -366,20 +367,21 @@ __global__ void __launch_bounds__(kThreads) rs_hist(const unsigned long long *ke
 // counted in element order (sub-round, warp, lane).
 __global__ void __launch_bounds__(kThreads) rs_scatter(const unsigned long long *kin, const int32_t *vin,
                                                       unsigned long long *kout, int32_t *vout, int64_t n,
-                                                      int shift, const uint32_t *base, int64_t nblk, Scalars *sc) {
-  __shared__ uint32_t run[16];
-  __shared__ uint32_t wc[kThreads / 32][16];
+                                                      int shift, const uint32_t *base, const uint32_t *sums,
+                                                      int64_t nblk, Scalars *sc) {
+  __shared__ uint32_t run[kDigits];
+  __shared__ uint32_t wc[kThreads / 32][kDigits];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x < 16) run[threadIdx.x] = base[threadIdx.x * nblk + blockIdx.x];
+  for (int e = threadIdx.x; e < kDigits; e += kThreads) run[e] = scanned(base, sums, e * nblk + blockIdx.x);
   const int64_t tb = blockIdx.x * (int64_t)kTile;
   for (int q = 0; q < kItems; ++q) {
     const int64_t i = tb + q * kThreads + threadIdx.x;
     const bool ok = i < n;
     const unsigned long long k = ok ? kin[i] : 0ull;
-    const int d = ok ? (int)((k >> shift) & 15u) : 16;
+    const int d = ok ? (int)((k >> shift) & (kDigits - 1u)) : kDigits;
     const unsigned peers = __match_any_sync(kFull, d);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (threadIdx.x < (kThreads / 32) * 16) wc[threadIdx.x >> 4][threadIdx.x & 15] = 0;
+    for (int e = threadIdx.x; e < (kThreads / 32) * kDigits; e += kThreads) wc[e / kDigits][e % kDigits] = 0;
     __syncthreads();
     if (ok && lane == __ffs(peers) - 1) wc[w][d] = __popc(peers);
     __syncthreads();
@@ -395,10 +397,10 @@ __global__ void __launch_bounds__(kThreads) rs_scatter(const unsigned long long 
       }
     }
     __syncthreads();
-    if (threadIdx.x < 16) {
+    for (int e = threadIdx.x; e < kDigits; e += kThreads) {
       uint32_t add = 0;
-      for (int u = 0; u < kThreads / 32; ++u) add += wc[u][threadIdx.x];
-      run[threadIdx.x] += add;
+      for (int u = 0; u < kThreads / 32; ++u) add += wc[u][e];
+      run[e] += add;
     }
     __syncthreads();
   }
@@ -435,7 +437,7 @@ __global__ void split_mark(const int32_t *L, int64_t nt, const double *dkey, con
 // the segments of the next round.  X holds the exclusive prefix count of left-going
 // triangles over the three concatenated lists; its differences are exact modulo 2^32.
 __global__ void split_move(const int32_t *Lin, int32_t *Lout, int64_t nt, const uint8_t *flag, const uint32_t *X,
-                           int32_t *seg_s, int32_t *seg_n, Scalars *sc) {
+                           const uint32_t *sums, int32_t *seg_s, int32_t *seg_n, Scalars *sc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t n = seg_n[i];
     const int64_t s = seg_s[i];
@@ -445,7 +447,7 @@ __global__ void split_move(const int32_t *Lin, int32_t *Lout, int64_t nt, const 
         Lout[c * nt + i] = tri;
         continue;
       }
-      const int64_t left_before = (int64_t)(uint32_t)(X[c * nt + i] - X[c * nt + s]);
+      const int64_t left_before = (int64_t)(uint32_t)(scanned(X, sums, c * nt + i) - scanned(X, sums, c * nt + s));
       const int64_t pos = flag[tri] ? s + left_before : s + n / 2 + (i - s - left_before);
       if (pos >= s && pos < s + n)
         Lout[c * nt + pos] = tri;
@@ -558,11 +560,11 @@ extern "C" int cbvh_build_device(cbvh_bvh *h, const float *verts_dev, const int3
     int32_t *vin = L0 + c * nt, *valt = tmpv;
     iota_kernel<<<grid(nt), 256, 0, s>>>(vin, nt);
     ++launches;
-    for (int shift = 0; shift < 64; shift += 4) {
-      if (((vary >> shift) & 15u) == 0) continue;  // every key has the same digit here
+    for (int shift = 0; shift < 64; shift += kDigitBits) {
+      if (((vary >> shift) & (kDigits - 1u)) == 0) continue;  // every key has the same digit here
       rs_hist<<<(unsigned)nblk, kThreads, 0, s>>>(kin, nt, shift, hist, nblk);
-      exclusive_scan(Plain{hist}, hist, 16 * nblk, sums, s, launches);
-      rs_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(kin, vin, kalt, valt, nt, shift, hist, nblk, sc);
+      exclusive_scan(Plain{hist}, hist, kDigits * nblk, sums, s, launches);
+      rs_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(kin, vin, kalt, valt, nt, shift, hist, sums, nblk, sc);
       launches += 2;
       std::swap(kin, kalt);
       std::swap(vin, valt);
@@ -580,7 +582,7 @@ extern "C" int cbvh_build_device(cbvh_bvh *h, const float *verts_dev, const int3
   for (int64_t width = 1; width < nt; width <<= 1) {  // ceil(log2 nt) rounds
     split_mark<<<grid(nt), 256, 0, s>>>(Lc, nt, dkey, seg_s, seg_n, flag);
     exclusive_scan(Gathered{Lc, flag}, X, 3 * nt, sums, s, launches);
-    split_move<<<grid(nt), 256, 0, s>>>(Lc, Ln, nt, flag, X, seg_s, seg_n, sc);
+    split_move<<<grid(nt), 256, 0, s>>>(Lc, Ln, nt, flag, X, sums, seg_s, seg_n, sc);
     launches += 2;
     std::swap(Lc, Ln);
   }
