@@ -18,7 +18,8 @@
 //      two or more triangles picks its axis of largest centroid extent (the ends of that
 //      axis's list), keeps the first half of that list on the left, and the other two lists
 //      follow by a stable partition (one prefix sum over all three lists per round), so
-//      each list stays sorted within every segment;
+//      each list stays sorted within every segment; once no segment holds more than 512
+//      triangles, the remaining rounds run segment by segment in shared memory;
 //   5. the leaves' triangles into the triangle table, then the refit kernels: leaf bounds,
 //      bounds bottom-up, predictor-corrector encoding top-down.
 #include <cuda_runtime.h>
@@ -204,12 +205,16 @@ __global__ void exponent_candidate(Scalars *sc, int headroom) {
   sc->ex1 = ilogb(M) - 29 + headroom;
 }
 
-// The exact test at e = ex1 - 1 and e = ex1: every lattice value of a vertex in use within
-// +-(2^(30 - headroom) - 1).  The rounded maximum is off by a few units in the last place
-// (its axis terms are exact), so the exact exponent is ex1 - 1, ex1 or ex1 + 1.
+// The test at e = ex1 - 1 and e = ex1: every lattice value of a vertex in use within
+// +-(2^(30 - headroom) - 1), that is |d.v| < 2^(e + 30 - headroom): below T0 = 2^ilogb(max)
+// and below T1 = 2T0.  The rounded maximum is off by a few units in the last place (its
+// axis terms are exact), so the exact exponent is ex1 - 1, ex1 or ex1 + 1.  The rounded
+// |d.v| (two additions of exact terms, off by at most 2^-51 (|a| + |b| + |c|)) decides every
+// value outside that margin of T0 and T1; the rest take the exact floor and ceil.
 __global__ void exponent_fits(const float *V, int64_t nv, int K, const uint8_t *used, Scalars *sc, int headroom) {
   const int ex1 = sc->ex1;
   const double inv0 = ldexp(1.0, -(ex1 - 1)), inv1 = ldexp(1.0, -ex1);
+  const double T0 = ldexp(1.0, ex1 - 1 + 30 - headroom), T1 = 2.0 * T0;
   const long long L = 1ll << (30 - headroom);
   bool f0 = false, f1 = false;
   const int64_t items = nv * K;
@@ -218,11 +223,29 @@ __global__ void exponent_fits(const float *V, int64_t nv, int K, const uint8_t *
     const int j = (int)(it - v * K);
     if (!used[v]) continue;
     const float p[3] = {V[3 * v], V[3 * v + 1], V[3 * v + 2]};
+    double a[3];
+    for (int c = 0; c < 3; ++c) a[c] = __dmul_rn((double)c_rdir[j][c], (double)p[c]);
+    const double s = fabs(__dadd_rn(__dadd_rn(a[0], a[1]), a[2]));
+    const double m = (fabs(a[0]) + fabs(a[1]) + fabs(a[2])) * 0x1p-51;
     long long lo, hi;
-    lattice_of(p, j, inv0, lo, hi);
-    f0 |= lo > L - 1 || hi < -(L - 1);
-    lattice_of(p, j, inv1, lo, hi);
-    f1 |= lo > L - 1 || hi < -(L - 1);
+    // rounding is monotone and T0, T1 are powers of two: fl(s + m) < T is certainly below,
+    // fl(s - m) > T certainly above
+    if (s + m >= T0) {
+      if (s - m > T0) {
+        f0 = true;
+      } else {
+        lattice_of(p, j, inv0, lo, hi);
+        f0 |= lo > L - 1 || hi < -(L - 1);
+      }
+      if (s + m >= T1) {
+        if (s - m > T1) {
+          f1 = true;
+        } else {
+          lattice_of(p, j, inv1, lo, hi);
+          f1 |= lo > L - 1 || hi < -(L - 1);
+        }
+      }
+    }
   }
   f0 = __any_sync(kFull, f0);
   f1 = __any_sync(kFull, f1);
@@ -466,6 +489,129 @@ __global__ void split_move(const int32_t *Lin, int32_t *Lout, int64_t nt, const 
   }
 }
 
+// The last rounds, on segments of at most kLocal triangles: one block per segment, all in
+// shared memory.  The segment is the one the global rounds left at position blockIdx.x of
+// their binary split tree (its path of halvings, left = 0); the lists become indices into
+// the segment's triangles (their keys staged beside them), and each round applies the same
+// axis rule and stable partition as split_mark / split_move, with a block-wide prefix sum.
+// Only list 0 is written back: after the last round all three lists agree.
+constexpr int kLocal = 512;
+__global__ void __launch_bounds__(kThreads) split_local(int32_t *L, int64_t nt, const double *dkey, int depth,
+                                                       int32_t *loc, Scalars *sc) {
+  __shared__ uint16_t ls[2][3][kLocal];
+  __shared__ int32_t tri[kLocal];
+  __shared__ double key[kLocal][3];
+  __shared__ uint8_t flag[kLocal];
+  __shared__ uint16_t ss[kLocal], sn[kLocal];
+  __shared__ uint16_t X[3 * kLocal];
+  __shared__ uint32_t wsum[kThreads / 32];
+  int64_t s = 0, n = nt;
+  for (int lev = depth - 1; lev >= 0; --lev) {
+    const int64_t h = n / 2;
+    if ((blockIdx.x >> lev) & 1u) {
+      s += h;
+      n -= h;
+    } else {
+      n = h;
+    }
+  }
+  if (n <= 1) return;  // one triangle (or none): nothing to split
+  if (n > kLocal) {
+    if (threadIdx.x == 0) atomicOr(&sc->flags, F_INTERNAL);
+    return;
+  }
+  const int m = (int)n;
+  for (int p = threadIdx.x; p < m; p += kThreads) {
+    const int32_t t = L[s + p];
+    tri[p] = t;
+    loc[t] = p;
+    for (int c = 0; c < 3; ++c) key[p][c] = dkey[3 * (int64_t)t + c];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += kThreads) {
+    ls[0][0][p] = (uint16_t)p;
+    for (int c = 1; c < 3; ++c) ls[0][c][p] = (uint16_t)loc[L[c * nt + s + p]];
+    ss[p] = 0;
+    sn[p] = (uint16_t)m;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int kPer = (3 * kLocal + kThreads - 1) / kThreads;  // scan entries per thread
+  int cur = 0;
+  for (int width = 1; width < m; width <<= 1) {
+    for (int p = threadIdx.x; p < m; p += kThreads) {
+      const int a = ss[p], len = sn[p];
+      if (len < 2) continue;
+      double ext[3];
+      for (int c = 0; c < 3; ++c) ext[c] = __dsub_rn(key[ls[cur][c][a + len - 1]][c], key[ls[cur][c][a]][c]);
+      int ax = 0;
+      if (ext[1] > ext[0]) ax = 1;
+      if (ext[2] > ext[ax]) ax = 2;
+      flag[ls[cur][ax][p]] = (p - a) < len / 2 ? 1 : 0;
+    }
+    __syncthreads();
+    // exclusive prefix count of left-going triangles over the three lists, in list order
+    uint32_t v[kPer], acc = 0;
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x * kPer + q;
+      v[q] = e < 3 * m ? flag[ls[cur][e / m][e % m]] : 0u;
+      acc += v[q];
+    }
+    uint32_t x = acc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t t = lane < kThreads / 32 ? wsum[lane] : 0u;
+      uint32_t incl = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane < kThreads / 32) wsum[lane] = incl - t;
+    }
+    __syncthreads();
+    uint32_t run = wsum[w] + x - acc;
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x * kPer + q;
+      if (e < 3 * m) X[e] = (uint16_t)run;
+      run += v[q];
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < m; p += kThreads) {
+      const int a = ss[p], len = sn[p];
+      for (int c = 0; c < 3; ++c) {
+        const uint16_t k = ls[cur][c][p];
+        if (len < 2) {
+          ls[cur ^ 1][c][p] = k;
+          continue;
+        }
+        const int lb = (int)X[c * m + p] - (int)X[c * m + a];
+        const int pos = flag[k] ? a + lb : a + len / 2 + (p - a - lb);
+        if (pos >= a && pos < a + len)
+          ls[cur ^ 1][c][pos] = k;
+        else
+          atomicOr(&sc->flags, F_INTERNAL);
+      }
+      if (len >= 2) {
+        const int half = len / 2;
+        if (p - a < half) {
+          sn[p] = (uint16_t)half;
+        } else {
+          ss[p] = (uint16_t)(a + half);
+          sn[p] = (uint16_t)(len - half);
+        }
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int p = threadIdx.x; p < m; p += kThreads) L[s + p] = tri[ls[cur][0][p]];
+}
+
 // ---------------------------------------------------------------- 5: triangle table
 __global__ void leaf_tris(const int32_t *perm, const int32_t *leaf_pos, int64_t nt, uint8_t *blob, int64_t off_tris) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nt; q += (int64_t)gridDim.x * blockDim.x)
@@ -579,13 +725,18 @@ extern "C" int cbvh_build_device(cbvh_bvh *h, const float *verts_dev, const int3
   seg_init<<<grid(nt), 256, 0, s>>>(seg_s, seg_n, nt);
   ++launches;
   int32_t *Lc = L0, *Ln = L1;
-  for (int64_t width = 1; width < nt; width <<= 1) {  // ceil(log2 nt) rounds
+  int depth = 0;  // global rounds until no segment holds more than kLocal triangles
+  for (; ((nt + (int64_t(1) << depth) - 1) >> depth) > kLocal; ++depth) {
     split_mark<<<grid(nt), 256, 0, s>>>(Lc, nt, dkey, seg_s, seg_n, flag);
     exclusive_scan(Gathered{Lc, flag}, X, 3 * nt, sums, s, launches);
     split_move<<<grid(nt), 256, 0, s>>>(Lc, Ln, nt, flag, X, sums, seg_s, seg_n, sc);
     launches += 2;
     std::swap(Lc, Ln);
   }
+  // the remaining rounds segment by segment in shared memory (tmpv, free after the sort,
+  // maps a triangle to its index in its segment)
+  split_local<<<(unsigned)(int64_t(1) << depth), kThreads, 0, s>>>(Lc, nt, dkey, depth, tmpv, sc);
+  ++launches;
 
   // 5: triangle table, then bounds and encoding with the refit kernels
   leaf_tris<<<grid(nt), 256, 0, s>>>(Lc, leaf_pos, nt, blob, h->off_tris);

@@ -21,22 +21,10 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
   err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
 }
 
-// floor(a + b + c) of the exact real sum.  Grow-Expansion (Shewchuk 1997) turns (a, b, c)
-// into a non-overlapping expansion q2 > q1 > q0 (by magnitude): if q2 has a fractional part,
-// the smaller components cannot move the sum across an integer, so the floor is q2's; if q2
-// is an integer the same holds one component down.
-__device__ long long floor3_exact(double a, double b, double c) {
-  // fast path: the rounded sum is off by at most 2u (|a| + |b| + |c|) (two additions, u =
-  // 2^-53); when twice that margin cannot reach an integer, its floor is the exact floor
-  const double sum = __dadd_rn(__dadd_rn(a, b), c);
-  const double slack = (fabs(a) + fabs(b) + fabs(c)) * 0x1p-51;
-  const double fl = floor(__dsub_rn(sum, slack));
-  if (fl == floor(__dadd_rn(sum, slack))) return (long long)fl;
-  double x1, y1;
-  two_sum(a, b, x1, y1);  // expansion [y1, x1]
-  double q, q0, q1, q2;
-  two_sum(c, y1, q, q0);
-  two_sum(q, x1, q2, q1);  // expansion [q0, q1, q2]
+// floor of the non-overlapping expansion q2 + q1 + q0 (decreasing magnitudes): when q2 has a
+// fractional part the smaller components cannot move the sum across an integer, so the
+// floor is q2's; when q2 is an integer the same holds one component down.
+__device__ __forceinline__ long long floor_expansion(double q2, double q1, double q0) {
   const double f2 = floor(q2);
   if (f2 != q2) return (long long)f2;
   const double f1 = floor(q1);
@@ -44,13 +32,27 @@ __device__ long long floor3_exact(double a, double b, double c) {
   return (long long)q2 + (long long)q1 + (long long)floor(q0);
 }
 
-// Lattice interval [floor, ceil] of d_j . v / 2^e for an FP32 vertex.
+// Lattice interval [floor, ceil] of d_j . v / 2^e for an FP32 vertex.  The three terms are
+// exact (a float times +-1 or 0 and a power of two).  When all three are integers -- the
+// usual case, since a float scaled into the lattice's range is an integer from 2^23 up --
+// their FP64 sum is exact and is both bounds.  Otherwise one Grow-Expansion serves floor
+// and ceil (the expansion of the negated sum is the negated expansion).
 __device__ __forceinline__ void lattice_of(const float *v, int j, double inv, long long &lo, long long &hi) {
   double t[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) t[c] = (double)c_rdir[j][c] * ((double)v[c] * inv);  // exact: scaling by 2^-e
-  lo = floor3_exact(t[0], t[1], t[2]);
-  hi = -floor3_exact(-t[0], -t[1], -t[2]);
+  if (floor(t[0]) == t[0] && floor(t[1]) == t[1] && floor(t[2]) == t[2] &&
+      fabs(t[0]) + fabs(t[1]) + fabs(t[2]) < 0x1p52) {
+    lo = hi = (long long)__dadd_rn(__dadd_rn(t[0], t[1]), t[2]);
+    return;
+  }
+  double x1, y1;
+  two_sum(t[0], t[1], x1, y1);  // expansion [y1, x1]
+  double q, q0, q1, q2;
+  two_sum(t[2], y1, q, q0);
+  two_sum(q, x1, q2, q1);  // expansion [q0, q1, q2]
+  lo = floor_expansion(q2, q1, q0);
+  hi = -floor_expansion(-q2, -q1, -q0);
 }
 
 }  // namespace

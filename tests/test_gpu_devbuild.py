@@ -39,8 +39,18 @@ def _signed_zero_terrain():
     return v, t
 
 
+def _box_corner(shift):
+    """A unit box moved so that its largest |d.v| is a power of two (shift 0.5: every
+    coordinate 0 or 1) or just below one (shift 0.5 - 2^-24: the far corner at 1 - 2^-24),
+    where the exponent search must decide exactly at the threshold."""
+    v, t = synth.box_mesh((1.0, 1.0, 1.0))
+    return (v.astype(np.float64) + shift).astype(np.float32), t
+
+
 MESHES = {
     "sphere": lambda: synth.icosphere(3, 1.0, 0.15, seed=9),
+    "box_pow2": lambda: _box_corner(0.5),
+    "box_below_pow2": lambda: _box_corner(0.5 - 2.0 ** -24),
     "terrain": lambda: synth.heightfield(32, 4.0, seed=4)[:2],
     "signed_zero": _signed_zero_terrain,
     "ragged_unused": lambda: (synth.icosphere(3, 1.0, 0.15, seed=3)[0], synth.icosphere(3, 1.0, 0.15, seed=3)[1][:1111]),
