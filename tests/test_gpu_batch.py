@@ -159,3 +159,18 @@ def test_arm_self_collision_against_oracle(cb, scene):
     assert checked > 600
     hits = np.stack(outs).any(0)
     assert 0 < hits.sum() < n  # some configurations fold onto themselves, some do not
+
+
+def test_batch_refuses_stream_vbyte_hierarchies(cb, scene):
+    """Stream VByte records vary in size; the batched kernels are compiled for fixed-size
+    records only, so a batch with such a hierarchy is refused before anything launches,
+    while the same hierarchy answers single queries."""
+    c1 = scene["c1"]
+    (va, ta), (vb, tb) = c1["A"], c1["B"]
+    A = cb.BVH(va, ta, 18, 4, cb.QUANT_SVB, 4096)
+    P = scene["P1"][:64]
+    with pytest.raises(cb.CbvhError) as e:
+        cb.Batch([dict(A=A, B=scene["S2"], kind="collide", poses=P)])
+    assert e.value.code == -1
+    want = cb.collide(scene["S1"], scene["S2"], P, pairs=False).hit.cpu().numpy()
+    assert (cb.collide(A, scene["S2"], P, pairs=False).hit.cpu().numpy() == want).all()
