@@ -213,7 +213,6 @@ __global__ void exponent_candidate(Scalars *sc, int headroom) {
 // value outside that margin of T0 and T1; the rest take the exact floor and ceil.
 __global__ void exponent_fits(const float *V, int64_t nv, int K, const uint8_t *used, Scalars *sc, int headroom) {
   const int ex1 = sc->ex1;
-  const double inv0 = ldexp(1.0, -(ex1 - 1)), inv1 = ldexp(1.0, -ex1);
   const double T0 = ldexp(1.0, ex1 - 1 + 30 - headroom), T1 = 2.0 * T0;
   const long long L = 1ll << (30 - headroom);
   bool f0 = false, f1 = false;
@@ -234,14 +233,14 @@ __global__ void exponent_fits(const float *V, int64_t nv, int K, const uint8_t *
       if (s - m > T0) {
         f0 = true;
       } else {
-        lattice_of(p, j, inv0, lo, hi);
+        lattice_of(p, j, ex1 - 1, lo, hi);
         f0 |= lo > L - 1 || hi < -(L - 1);
       }
       if (s + m >= T1) {
         if (s - m > T1) {
           f1 = true;
         } else {
-          lattice_of(p, j, inv1, lo, hi);
+          lattice_of(p, j, ex1, lo, hi);
           f1 |= lo > L - 1 || hi < -(L - 1);
         }
       }

@@ -72,7 +72,6 @@ struct RefitArgs {
   const int32_t *tris;
   int64_t n_verts, n_tris;
   int K, bits, e;
-  double inv;   // 2^-e
   float scale;  // 2^e
   const uint64_t *rec_off;  // [nn] byte offset of the node's record
   const int32_t *parent;    // [nn] blob-order index of the parent, -1 at the root
@@ -103,7 +102,7 @@ __global__ void vertex_lattice(const RefitArgs a) {
       continue;
     }
     long long lo, hi;
-    lattice_of(p, j, a.inv, lo, hi);
+    lattice_of(p, j, a.e, lo, hi);
     // clamp to the int32 range; anything beyond the lattice's 2^30 fails at the leaf
     out[0] = (int32_t)max(min(lo, (long long)INT32_MAX), (long long)INT32_MIN);
     out[1] = (int32_t)max(min(hi, (long long)INT32_MAX), (long long)INT32_MIN);
@@ -392,7 +391,6 @@ int refit_launch(cbvh_bvh *h, const float *verts_dev, const int32_t *tris_dev, u
   a.K = h->K;
   a.bits = h->bits;
   a.e = h->e;
-  a.inv = std::ldexp(1.0, -h->e);
   a.scale = std::ldexp(1.0f, h->e);
   a.rec_off = reinterpret_cast<const uint64_t *>(ws + L.rec_off);
   a.parent = reinterpret_cast<const int32_t *>(ws + L.parent);
