@@ -40,6 +40,7 @@ extern "C" {
 #define CBVH_ERR_TIMEOUT (-6)   /* device: a bounded wait or the traversal step cap ran out */
 #define CBVH_ERR_WORKSPACE (-7) /* workspace smaller than cbvh_workspace_bytes() */
 #define CBVH_ERR_STATE (-9)     /* handle has no device blob attached */
+#define CBVH_ERR_IO (-10)       /* a file could not be read or written, or is not a valid hierarchy */
 
 /* collide flags */
 #define CBVH_QUANT_FP16 1 /* quant_bits value of the half-precision descriptor mode */
@@ -99,6 +100,23 @@ int cbvh_info(const cbvh_bvh *h, cbvh_info_t *out);
 
 /* The host copy of the blob (read-only, owned by the handle, valid until cbvh_free). */
 int cbvh_blob_host(const cbvh_bvh *h, const uint8_t **blob_host, int64_t *bytes);
+
+/* Write a hierarchy to a file: a 16-byte header (magic "CBVF", format version 1, the
+ * vertex count as int64) followed by the blob bytes of cbvh_blob_host.  Errors:
+ * CBVH_ERR_ARG (NULL), CBVH_ERR_STATE (a plan without geometry, or a host copy left stale
+ * by a device build), CBVH_ERR_IO. */
+int cbvh_save(const cbvh_bvh *h, const char *path);
+/* Read a hierarchy written by cbvh_save into a new handle (host memory only; attach it
+ * before querying).  The blob is checked completely before it is accepted, so that no
+ * kernel can read outside it:
+ *   - the header's fields against the build rules;
+ *   - the treelet offsets (ordered, inside the blob);
+ *   - every record's parent, children, leaf slot and depth;
+ *   - the offset tables of Stream VByte treelets;
+ *   - the triangle table's indices.
+ * Errors: CBVH_ERR_ARG (NULL), CBVH_ERR_IO (unreadable, or not a valid hierarchy, with the
+ * first failed check in cbvh_last_error). */
+int cbvh_load(const char *path, cbvh_bvh **out);
 
 /* Copy the blob into caller-owned device memory `dev_blob` (>= blob_bytes, 256-byte
  * aligned) on `stream` and remember that address for queries.  The caller keeps the buffer

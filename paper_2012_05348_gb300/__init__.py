@@ -27,7 +27,7 @@ LIB_PATH = _build.LIB
 EARLY_EXIT = 1
 SORT_PAIRS = 2
 ERR = {0: "OK", -1: "ARG", -2: "MESH", -3: "CUDA", -4: "CAPACITY", -5: "STACK", -6: "TIMEOUT", -7: "WORKSPACE",
-       -9: "STATE"}
+       -9: "STATE", -10: "IO"}
 
 
 
@@ -65,6 +65,8 @@ def _declare(L):
     L.cbvh_refit_prepare.argtypes = [P, P, I64, P]
     L.cbvh_refit.argtypes = [P, P, I64, P, P, I64, P, P]
     L.cbvh_build_plan.argtypes = [I64, I64, I32, I32, I32, I32, C.POINTER(P)]
+    L.cbvh_save.argtypes = [P, C.c_char_p]
+    L.cbvh_load.argtypes = [C.c_char_p, C.POINTER(P)]
     L.cbvh_build_device_workspace_bytes.argtypes = [P, C.POINTER(I64)]
     L.cbvh_build_device.argtypes = [P, P, P, P, I64, U32, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
@@ -72,7 +74,8 @@ def _declare(L):
               "cbvh_profile_collect", "cbvh_distance_noalloc", "cbvh_batch_create", "cbvh_batch_free",
               "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option",
               "cbvh_kernel_launches", "cbvh_refit_workspace_bytes", "cbvh_refit_prepare", "cbvh_refit",
-              "cbvh_build_plan", "cbvh_build_device_workspace_bytes", "cbvh_build_device"):
+              "cbvh_build_plan", "cbvh_build_device_workspace_bytes", "cbvh_build_device", "cbvh_save",
+              "cbvh_load"):
         getattr(L, f).restype = I32
     return L
 
@@ -158,6 +161,26 @@ class BVH:
                                        C.byref(h)))
         self._h = h
         self.n_verts = int(n_verts)
+        self._refresh_info()
+        self.blob_dev = None
+        if device is not None:
+            self.attach(device)
+        return self
+
+    def save(self, path: str) -> None:
+        """cbvh_save: the hierarchy (its host blob and vertex count) to a file."""
+        _check(_load().cbvh_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        """cbvh_load: a hierarchy written by save, checked before it is accepted, attached
+        to `device` (None: host only)."""
+        self = cls.__new__(cls)
+        h = C.c_void_p()
+        _check(_load().cbvh_load(os.fsencode(path), C.byref(h)))
+        self._h = h
+        with open(path, "rb") as f:
+            self.n_verts = int.from_bytes(f.read(16)[8:16], "little", signed=True)
         self._refresh_info()
         self.blob_dev = None
         if device is not None:

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <limits>
@@ -688,6 +689,196 @@ extern "C" int cbvh_build_plan(int64_t n_verts, int64_t n_tris, int k, int branc
   }
   h->headroom = cbvh::lattice_headroom();
   h->geometry = false;
+  *out = h;
+  return CBVH_OK;
+}
+
+namespace {
+uint16_t rd16(const std::vector<uint8_t> &b, int64_t o) {
+  uint16_t v;
+  std::memcpy(&v, &b[o], 2);
+  return v;
+}
+uint32_t rd32(const std::vector<uint8_t> &b, int64_t o) {
+  uint32_t v;
+  std::memcpy(&v, &b[o], 4);
+  return v;
+}
+uint64_t rd64(const std::vector<uint8_t> &b, int64_t o) {
+  uint64_t v;
+  std::memcpy(&v, &b[o], 8);
+  return v;
+}
+
+// Checks every part of a blob the kernels rely on and fills the handle's fields from its
+// header.  Returns "" or the first failed check.
+std::string check_blob(const std::vector<uint8_t> &b, cbvh_bvh *h) {
+  const int64_t n = (int64_t)b.size();
+  if (n < 64) return "shorter than its header";
+  if (rd32(b, 0) != 0x48564243u || rd16(b, 4) != 1) return "not a version-1 hierarchy blob";
+  const int k = b[6], K = b[7], m = b[8], bits = b[9], lbits = b[10], max_td = b[11];
+  const int e = (int32_t)rd32(b, 12);
+  const int64_t nt = rd32(b, 16), nn = rd32(b, 20), ntl = rd32(b, 24);
+  const int rec = (int)rd32(b, 28), root = (int)rd32(b, 32), tb = (int)rd32(b, 36);
+  const int depth = (int)rd32(b, 40), packing = (int)rd32(b, 44);
+  const int64_t off_tris = (int64_t)rd64(b, 48), total = (int64_t)rd64(b, 56);
+  if ((k != 6 && k != 18 && k != 24 && k != 26) || K != k / 2) return "bad k";
+  if (m != 2 && m != 4 && m != 8 && m != 16) return "bad branching";
+  if (bits != 0 && bits != CBVH_QUANT_FP16 && bits != CBVH_QUANT_SVB && bits != 8 && bits != 16)
+    return "bad quant_bits";
+  if (tb < 4096 || tb > 131072 || (tb & (tb - 1))) return "bad treelet budget";
+  if (packing != CBVH_PACK_TOP_DOWN && packing != CBVH_PACK_BOTTOM_UP) return "bad treelet packing";
+  if (e < -120 || e > 96) return "bad lattice exponent";
+  int want_root = 8 + 8 * K, want_rec;
+  if (bits == CBVH_QUANT_FP16)
+    want_root = want_rec = 8 + 4 * K;
+  else if (bits == CBVH_QUANT_SVB)
+    want_rec = 16 + 8 * K;
+  else
+    want_rec = bits == 0 ? want_root : (8 + 2 * K * (bits / 8) + 3) / 4 * 4;
+  if (rec != want_rec || root != want_root) return "record sizes do not match the mode";
+  if (nt < 1 || nn < 1 || ntl < 1 || nn < nt) return "bad counts";
+  if (lbits < 1 || lbits > 16 || (uint64_t)ntl >= ((uint64_t)1 << (32 - lbits))) return "bad node reference split";
+  if (total != n) return "size does not match the header";
+  const int64_t tab_end = 64 + 8 * (ntl + 1);
+  if (tab_end > n) return "treelet table outside the blob";
+  std::vector<int64_t> toff(ntl + 1);
+  for (int64_t t = 0; t <= ntl; ++t) toff[t] = (int64_t)rd64(b, 64 + 8 * t);
+  if (toff[0] != (tab_end + 15) / 16 * 16) return "first treelet misplaced";
+  for (int64_t t = 0; t < ntl; ++t)
+    if (toff[t + 1] <= toff[t] || (toff[t] & 15) || toff[t + 1] > n) return "treelet offsets out of order";
+  if (toff[ntl] != off_tris || off_tris + 48 * nt != total) return "triangle table misplaced";
+  const bool svb = bits == CBVH_QUANT_SVB;
+  // depth of each treelet's root, from the external references (each treelet but the first
+  // is referenced exactly once, by a node of an earlier treelet)
+  std::vector<int> troot_depth(ntl, -1);
+  troot_depth[0] = 0;
+  std::vector<uint8_t> slot_used(nt, 0);
+  int64_t nodes = 0, leaves = 0;
+  int max_depth = 0, max_tdepth = 0;
+  for (int64_t t = 0; t < ntl; ++t) {
+    const int64_t T = toff[t], size = toff[t + 1] - T;
+    if (size < 16) return "treelet too small";
+    const int64_t cnt = rd32(b, T);
+    if (cnt < 1 || cnt >= ((int64_t)1 << lbits)) return "bad treelet node count";
+    if ((int64_t)rd32(b, T + 4) != nodes) return "treelet header: wrong first-node index";
+    if (troot_depth[t] < 0) return "treelet not referenced by its parent";
+    std::vector<int64_t> pos(cnt);
+    if (svb) {
+      const int64_t first = 16 + (2 * cnt + 7) / 8 * 8;
+      if (first + root > size) return "treelet too small for its offset table";
+      int64_t end = 0;
+      for (int64_t l = 0; l < cnt; ++l) {
+        const int64_t o = 4 * (int64_t)rd16(b, T + 16 + 2 * l);
+        if ((l == 0 && o != first) || (l > 0 && o < end) || o + (l ? 16 : root) > size) return "bad record offset";
+        pos[l] = o;
+        if (l == 0) {
+          end = o + root;
+        } else {  // the record's deltas, by its control word, stay before the next record
+          const uint64_t ctl = rd64(b, T + o + 8);
+          int64_t bytes = 16;
+          for (int i = 0; i < 2 * K; ++i) bytes += (int64_t)((ctl >> (2 * i)) & 3u) + 1;
+          end = o + (bytes + 3) / 4 * 4;
+          if (end > size) return "record runs past its treelet";
+        }
+      }
+    } else {
+      if (16 + root + (cnt - 1) * (int64_t)rec > size) return "treelet too small for its records";
+      for (int64_t l = 0; l < cnt; ++l) pos[l] = 16 + (l ? root + (l - 1) * (int64_t)rec : 0);
+    }
+    std::vector<int> td(cnt, 0);
+    for (int64_t l = 0; l < cnt; ++l) {
+      const uint32_t w0 = rd32(b, T + pos[l]), w1 = rd32(b, T + pos[l] + 4);
+      const uint32_t par = w0 & 0xffffu, nc = (w0 >> 16) & 31u, ext = (w0 >> 21) & 1u, d = w0 >> 24;
+      if (l == 0 ? (par != 0xffffu || d != 0) : (par >= (uint32_t)l || d != (uint32_t)td[par] + 1))
+        return "bad parent or depth";
+      if (((w0 >> 22) & 3u) != 0 || nc > (uint32_t)m) return "bad child count";
+      td[l] = (int)d;
+      max_tdepth = std::max(max_tdepth, (int)d);
+      const int node_depth = troot_depth[t] + (int)d;
+      max_depth = std::max(max_depth, node_depth);
+      if (nc == 0) {
+        if (ext || w1 >= (uint64_t)nt || slot_used[w1]) return "bad leaf slot";
+        slot_used[w1] = 1;
+        ++leaves;
+      } else if (ext) {
+        if ((uint64_t)w1 + nc > (uint64_t)ntl || w1 <= (uint64_t)t) return "bad child treelet";
+        for (uint32_t c = 0; c < nc; ++c) {
+          if (troot_depth[w1 + c] >= 0) return "treelet referenced twice";
+          troot_depth[w1 + c] = node_depth + 1;
+        }
+      } else if (w1 <= (uint64_t)l || (uint64_t)w1 + nc > (uint64_t)cnt) {
+        return "bad child index";
+      }
+    }
+    nodes += cnt;
+  }
+  if (nodes != nn || leaves != nt) return "node or leaf count does not match the header";
+  if (max_depth != depth || max_tdepth != max_td) return "depths do not match the header";
+  for (int64_t i = 0; i < nt; ++i)
+    if (rd32(b, off_tris + 48 * i + 12) >= (uint64_t)nt) return "bad triangle index";
+  h->k = k;
+  h->K = K;
+  h->m = m;
+  h->bits = bits;
+  h->treelet_bytes = tb;
+  h->e = e;
+  h->lbits = lbits;
+  h->max_tdepth = max_td;
+  h->depth = depth;
+  h->rec_bytes = rec;
+  h->root_bytes = root;
+  h->n_tris = nt;
+  h->n_nodes = nn;
+  h->n_treelets = ntl;
+  h->off_treelets = toff[0];
+  h->off_tris = off_tris;
+  return "";
+}
+}  // namespace
+
+extern "C" int cbvh_save(const cbvh_bvh *h, const char *path) {
+  cbvh::clear_error();
+  if (!h || !path) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  if (!h->geometry) return cbvh::fail(CBVH_ERR_STATE, "a plan has no geometry to save");
+  if (h->host_stale)
+    return cbvh::fail(CBVH_ERR_STATE, "host blob not updated by the device build (CBVH_BUILD_HOST_COPY not given)");
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return cbvh::fail(CBVH_ERR_IO, std::string("cannot open ") + path + " for writing");
+  uint8_t head[16] = {'C', 'B', 'V', 'F', 1, 0, 0, 0};
+  const int64_t nv = h->n_verts;
+  std::memcpy(head + 8, &nv, 8);
+  bool ok = std::fwrite(head, 1, 16, f) == 16 && std::fwrite(h->blob.data(), 1, h->blob.size(), f) == h->blob.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? CBVH_OK : cbvh::fail(CBVH_ERR_IO, std::string("cannot write ") + path);
+}
+
+extern "C" int cbvh_load(const char *path, cbvh_bvh **out) {
+  cbvh::clear_error();
+  if (!path || !out) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return cbvh::fail(CBVH_ERR_IO, std::string("cannot open ") + path);
+  std::vector<uint8_t> data;
+  uint8_t buf[1 << 16];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) data.insert(data.end(), buf, buf + got);
+  const bool err = std::ferror(f) != 0;
+  std::fclose(f);
+  if (err) return cbvh::fail(CBVH_ERR_IO, std::string("cannot read ") + path);
+  if (data.size() < 16 || std::memcmp(data.data(), "CBVF\x01\0\0\0", 8) != 0)
+    return cbvh::fail(CBVH_ERR_IO, "not a saved hierarchy (bad file header)");
+  int64_t nv;
+  std::memcpy(&nv, data.data() + 8, 8);
+  auto h = new cbvh_bvh();
+  h->blob.assign(data.begin() + 16, data.end());
+  const std::string why = check_blob(h->blob, h);
+  if (!why.empty() || nv < 3 || nv > 0x7fffffff) {
+    delete h;
+    return cbvh::fail(CBVH_ERR_IO, "invalid hierarchy file: " + (why.empty() ? std::string("bad vertex count") : why));
+  }
+  h->n_verts = nv;
+  h->geometry = true;
   *out = h;
   return CBVH_OK;
 }

@@ -370,3 +370,20 @@ def test_kernel_launch_counter(cb, c1):
     cb.distance(c1["A"], c1["B"], P)
     n2 = cb.kernel_launches()
     assert n1 - n0 == 4 and n2 - n1 == 12
+
+
+def test_loaded_hierarchy_answers_like_the_original(cb, c1, tmp_path):
+    """cbvh_save / cbvh_load: the loaded blob is the saved one, so every query agrees."""
+    A = cb.BVH.load(_save_to(c1["A"], tmp_path / "a.cbvh"))
+    B = cb.BVH.load(_save_to(c1["B"], tmp_path / "b.cbvh"))
+    P = _gpu(c1["P"][:128])
+    r0, r1 = cb.collide(c1["A"], c1["B"], P), cb.collide(A, B, P)
+    assert (r0.hit.cpu().numpy() == r1.hit.cpu().numpy()).all()
+    assert (r0.offsets.cpu().numpy() == r1.offsets.cpu().numpy()).all()
+    assert (r0.pairs.cpu().numpy() == r1.pairs.cpu().numpy()).all()
+    assert (cb.distance(c1["A"], c1["B"], P).cpu().numpy() == cb.distance(A, B, P).cpu().numpy()).all()
+
+
+def _save_to(h, path):
+    h.save(str(path))
+    return str(path)
