@@ -25,6 +25,14 @@ import numpy as np
 from . import Batch, CbvhError, _torch
 
 
+def combine(kind: str, parts: list) -> np.ndarray:
+    """One configuration's result from its links' results: a chain collides when any link
+    does (largest flag), and its distance is the smallest over the links."""
+    if len(parts) == 1:
+        return np.array(parts[0], copy=True)
+    return np.maximum.reduce(parts) if kind == "collide" else np.minimum.reduce(parts)
+
+
 class Request:
     __slots__ = ("env", "robot", "kind", "poses", "early_exit", "future", "t_submit", "t_done")
 
@@ -121,14 +129,7 @@ class Server:
             if code != 0:
                 r.future.set_exception(CbvhError(code, "device status"))
                 continue
-            vals = [o.numpy() for o in parts]
-            if len(vals) == 1:
-                res = vals[0].copy()
-            elif r.kind == "collide":
-                res = np.maximum.reduce(vals)
-            else:
-                res = np.minimum.reduce(vals)
-            r.future.set_result(res)
+            r.future.set_result(combine(r.kind, [o.numpy() for o in parts]))
         self.busy[slot] = None
         self.used -= nbytes
 
