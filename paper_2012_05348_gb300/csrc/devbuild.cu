@@ -210,7 +210,8 @@ __global__ void exponent_candidate(Scalars *sc, int headroom) {
 // and below T1 = 2T0.  The rounded maximum is off by a few units in the last place (its
 // axis terms are exact), so the exact exponent is ex1 - 1, ex1 or ex1 + 1.  The rounded
 // |d.v| (two additions of exact terms, off by at most 2^-51 (|a| + |b| + |c|)) decides every
-// value outside that margin of T0 and T1; the rest take the exact floor and ceil.
+// value outside that margin of T0 and T1; the rest take the exact floor and ceil.  Most
+// values never reach FP64: their terms are integers at the lattice's scale.
 __global__ void exponent_fits(const float *V, int64_t nv, int K, const uint8_t *used, Scalars *sc, int headroom) {
   const int ex1 = sc->ex1;
   const double T0 = ldexp(1.0, ex1 - 1 + 30 - headroom), T1 = 2.0 * T0;
@@ -222,6 +223,24 @@ __global__ void exponent_fits(const float *V, int64_t nv, int K, const uint8_t *
     const int j = (int)(it - v * K);
     if (!used[v]) continue;
     const float p[3] = {V[3 * v], V[3 * v + 1], V[3 * v + 2]};
+    // usual case: the terms at scale 2^-(ex1 - 1) are integers and S, their int64 sum, is
+    // exact; e = ex1 - 1 fits iff |S| <= L - 1 and e = ex1 iff |S / 2| < L
+    long long S = 0;
+    bool ints = true;
+    for (int c = 0; c < 3; ++c) {
+      const int d = c_rdir[j][c];
+      long long x;
+      if (d != 0) {
+        ints = ints && scaled_int(p[c], ex1 - 1, x);
+        S += ints ? d * x : 0;
+      }
+    }
+    if (ints) {
+      const long long aS = S < 0 ? -S : S;
+      f0 |= aS > L - 1;
+      f1 |= aS >= 2 * L;
+      continue;
+    }
     double a[3];
     for (int c = 0; c < 3; ++c) a[c] = __dmul_rn((double)c_rdir[j][c], (double)p[c]);
     const double s = fabs(__dadd_rn(__dadd_rn(a[0], a[1]), a[2]));
