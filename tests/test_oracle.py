@@ -221,6 +221,85 @@ def test_encoding_invariants(k, m, bits, tb, packing):
         assert (pl["treelet"][rn] == np.arange(len(rn))).all()
 
 
+def _adjacent_f32(decf, L, e):
+    """decf[..., 0] is the largest FP32 value <= L_lo 2^e and decf[..., 1] the smallest >=
+    L_hi 2^e (exact comparisons: |L| < 2^31, so L 2^e and every FP32 value are exact in FP64)."""
+    lo, hi = decf[..., 0], decf[..., 1]
+    xlo = np.ldexp(L[..., 0].astype(np.float64), e)
+    xhi = np.ldexp(L[..., 1].astype(np.float64), e)
+    up = np.nextafter(lo, np.float32(np.inf)).astype(np.float64)
+    dn = np.nextafter(hi, np.float32(-np.inf)).astype(np.float64)
+    assert (lo.astype(np.float64) <= xlo).all() and (up > xlo).all()
+    assert (hi.astype(np.float64) >= xhi).all() and (dn < xhi).all()
+
+
+def _predictor_corrector_mesh(kind):
+    if kind == "sphere":
+        return synth.icosphere(3, 1.0, 0.15, seed=5)
+    # adversarial: coordinates on a coarse power-of-two grid, so that many parent ranges
+    # sit exactly at (2^b - 1) 2^s and at powers of two, where an off-by-one in the shift
+    # or in a corrector's rounding shows
+    rng = np.random.default_rng(41)
+    n = 300
+    c = rng.integers(-64, 64, size=(n, 1, 3)).astype(np.float64)
+    v = (c + rng.integers(-5, 6, size=(n, 3, 3))) * 2.0 ** -5
+    v[:, 2] += 2.0 ** -9  # keep every triangle non-degenerate
+    v = v.reshape(-1, 3).astype(np.float32)
+    return v, np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+
+
+@pytest.mark.parametrize("mesh", ["sphere", "grid"])
+@pytest.mark.parametrize("packing", [oracle.PACKING_TOP_DOWN, oracle.PACKING_BOTTOM_UP])
+@pytest.mark.parametrize("k,m,bits,tb", [(24, 8, 8, 16384), (18, 4, 16, 4096), (6, 2, 8, 4096), (26, 16, 8, 8192),
+                                         (18, 4, 0, 4096), (18, 4, 2, 4096), (24, 8, 16, 65536)])
+def test_predictor_corrector_against_its_definition(k, m, bits, tb, packing, mesh):
+    """The encoder's shift, correctors and decoded intervals, recomputed top-down from the
+    node's exact lattice interval C and the parent's decoded interval P, as the abstract and
+    Sec. III-B describe them (the prediction is the parent's decoded bounds, the correction a
+    small outward integer delta):
+      s     = smallest s >= 0 with (P_hi - P_lo) >> s <= 2^b - 1, i.e. max(0, bitlen - b);
+      d_lo  = floor((C_lo - P_lo) / 2^s),  d_hi = floor((P_hi - C_hi) / 2^s);
+      C'    = [P_lo + d_lo 2^s, P_hi - d_hi 2^s]  (the tightest such interval around C).
+    Treelet roots are absolute (exact); FP32 and FP16 records are absolute; Stream VByte
+    records hold the unshifted exact deltas.  The decoded FP32 bounds are the adjacent
+    floats: lo the largest FP32 <= C'_lo 2^e, hi the smallest >= C'_hi 2^e."""
+    v, t = _predictor_corrector_mesh(mesh)
+    h = oracle.BVH(v, t, k, m, bits, tb, packing=packing)
+    tr, L, pl = h.tree(), h.lattice(), h.placement()
+    ex, dec, decf, delta = L["exact"], L["decoded"], L["decf"], pl["delta"]
+    par, local = tr["parent"], pl["local"]
+    K = k // 2
+    want_dec = np.empty_like(ex)
+    want_delta = np.zeros_like(delta)
+    for x in range(h.n_nodes):  # parents precede their children in node order
+        C = [(int(ex[x, j, 0]), int(ex[x, j, 1])) for j in range(K)]
+        if local[x] == 0 or bits in (0, 1):
+            want_dec[x] = ex[x]
+            continue
+        assert par[x] < x
+        for j in range(K):
+            P_lo, P_hi = int(want_dec[par[x], j, 0]), int(want_dec[par[x], j, 1])
+            C_lo, C_hi = C[j]
+            assert P_lo <= C_lo <= C_hi <= P_hi
+            if bits == oracle.QUANT_SVB:
+                want_delta[x, j] = (C_lo - P_lo, P_hi - C_hi)
+                want_dec[x, j] = (C_lo, C_hi)
+                continue
+            s = max(0, (P_hi - P_lo).bit_length() - bits)
+            assert (P_hi - P_lo) >> s <= (1 << bits) - 1 and (s == 0 or (P_hi - P_lo) >> (s - 1) > (1 << bits) - 1)
+            d_lo, d_hi = (C_lo - P_lo) // 2 ** s, (P_hi - C_hi) // 2 ** s
+            lo, hi = P_lo + d_lo * 2 ** s, P_hi - d_hi * 2 ** s
+            # outward, and one more step of 2^s inward would cut the exact interval
+            assert lo <= C_lo < lo + 2 ** s and hi - 2 ** s < C_hi <= hi
+            want_delta[x, j] = (d_lo, d_hi)
+            want_dec[x, j] = (lo, hi)
+    assert (dec == want_dec).all()
+    if bits >= 8 or bits == oracle.QUANT_SVB:
+        assert (delta == want_delta).all()
+    if bits != oracle.QUANT_FP16:  # FP16 rounding has its own pin below
+        _adjacent_f32(decf, want_dec, h.e)
+
+
 def _golden_svb():
     path = os.path.join(os.path.dirname(__file__), "golden", "stream_vbyte.txt")
     cases = []
