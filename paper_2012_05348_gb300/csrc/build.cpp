@@ -787,11 +787,16 @@ std::string check_blob(const std::vector<uint8_t> &b, cbvh_bvh *h) {
       for (int64_t l = 0; l < cnt; ++l) pos[l] = 16 + (l ? root + (l - 1) * (int64_t)rec : 0);
     }
     std::vector<int> td(cnt, 0);
+    // the node whose child range holds each node of the treelet: the decode walks a node's
+    // chain through its parent field, so that field must name the node that references it,
+    // and no node may be referenced twice
+    std::vector<int64_t> owner(cnt, -1);
     for (int64_t l = 0; l < cnt; ++l) {
       const uint32_t w0 = rd32(b, T + pos[l]), w1 = rd32(b, T + pos[l] + 4);
       const uint32_t par = w0 & 0xffffu, nc = (w0 >> 16) & 31u, ext = (w0 >> 21) & 1u, d = w0 >> 24;
       if (l == 0 ? (par != 0xffffu || d != 0) : (par >= (uint32_t)l || d != (uint32_t)td[par] + 1))
         return "bad parent or depth";
+      if (l > 0 && owner[l] != (int64_t)par) return "parent field does not name the referencing node";
       if (((w0 >> 22) & 3u) != 0 || nc > (uint32_t)m) return "bad child count";
       td[l] = (int)d;
       max_tdepth = std::max(max_tdepth, (int)d);
@@ -809,6 +814,11 @@ std::string check_blob(const std::vector<uint8_t> &b, cbvh_bvh *h) {
         }
       } else if (w1 <= (uint64_t)l || (uint64_t)w1 + nc > (uint64_t)cnt) {
         return "bad child index";
+      } else {
+        for (uint32_t c = 0; c < nc; ++c) {
+          if (owner[w1 + c] >= 0) return "node referenced twice";
+          owner[w1 + c] = l;
+        }
       }
     }
     nodes += cnt;

@@ -156,6 +156,29 @@ def _mutations(blob, bits):
             break
     if ext_rec is not None:
         mut("child treelet", lambda b: b[ext_rec + 4:ext_rec + 8].view(np.uint32).__setitem__(0, ntl))
+    # two inner records of one treelet at the same depth with local children: re-parent a
+    # child of the second to the first (depths stay consistent), and point the second's
+    # child range at the first's (its nodes would be referenced twice)
+    pair = None
+    for T, cnt, offs in recs:
+        by_depth = {}
+        for l in range(cnt):
+            w0, w1 = (int(x) for x in blob[T + offs[l]:T + offs[l] + 8].view(np.uint32))
+            if (w0 >> 16) & 31 and not (w0 >> 21) & 1:
+                by_depth.setdefault(w0 >> 24, []).append((l, w1))
+        for d, ls in sorted(by_depth.items()):
+            if len(ls) >= 2:
+                pair = (T, offs, ls[0], ls[1])
+                break
+        if pair is not None:
+            break
+    if pair is not None:
+        T, offs, (l1, c1), (l2, c2) = pair
+        R = T + offs[c2]
+        mut("child's parent field", lambda b: b[R:R + 4].view(np.uint32).__setitem__(
+            0, (int(b[R:R + 4].view(np.uint32)[0]) & ~0xffff) | l1))
+        R2 = T + offs[l2]
+        mut("child referenced twice", lambda b: b[R2 + 4:R2 + 8].view(np.uint32).__setitem__(0, c1))
     if len(offs0) > 1:
         R = T0 + offs0[1]
         mut("parent", lambda b: b[R:R + 4].view(np.uint32).__setitem__(
@@ -182,7 +205,7 @@ def test_each_damaged_field_is_refused(cb, tmp_path, bits):
     _write(str(tmp_path / "head.cbvh"), bytes(bad_head), blob)
     _refused(cb, str(tmp_path / "head.cbvh"))
     muts = _mutations(blob, bits)
-    assert len(muts) >= 14
+    assert len(muts) >= 16
     for name, b in muts:
         p = str(tmp_path / f"m_{name.replace(' ', '_')}.cbvh")
         _write(p, head, b)
