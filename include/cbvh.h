@@ -37,7 +37,7 @@ extern "C" {
 #define CBVH_ERR_CUDA (-3)      /* a CUDA runtime call failed; see cbvh_last_error() */
 #define CBVH_ERR_CAPACITY (-4)  /* device: more intersecting pairs than pair_capacity */
 #define CBVH_ERR_STACK (-5)     /* device: traversal stack bound exceeded (never by construction) */
-#define CBVH_ERR_TIMEOUT (-6)   /* device: a bounded wait or the traversal step cap ran out */
+#define CBVH_ERR_TIMEOUT (-6)   /* device: a bounded wait ran out (CBVH_OPT_WAIT_CAP); results are incomplete */
 #define CBVH_ERR_WORKSPACE (-7) /* workspace smaller than cbvh_workspace_bytes() */
 #define CBVH_ERR_STATE (-9)     /* handle has no device blob attached */
 #define CBVH_ERR_IO (-10)       /* a file could not be read or written, or is not a valid hierarchy */
@@ -166,10 +166,17 @@ int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int6
  * query time -- for example a planner's control loop that must never block on the device
  * allocator once it runs, or a plug-in whose host application owns all device memory.
  * The paper has no counterpart; it is a packaging of the same query.
+ *   Schedule: cbvh_distance's two passes (early-exit collision, then branch and bound) with
+ *   its work mapping and budgets (CBVH_OPT_SPLIT, CBVH_OPT_BUDGET0), run over chunks of at
+ *   most 2^20 poses.
  *   Scratch: a fixed 32 MiB array inside the library, reserved on every GPU that loads it
- *   until the process exits.  It holds the query's counters, its task buffers and one
- *   node-pair stack per warp; pairs of hierarchies whose stack bound leaves room for fewer
- *   than 4 warps are rejected with CBVH_ERR_WORKSPACE and a message giving the bytes needed.
+ *   until the process exits.  It holds the query's counters, the intersection flags of one
+ *   chunk, two task buffers of 2^17 entries (cbvh_distance's workspace holds at least 2^22;
+ *   tasks that find the buffer full run on where they are, which is slower on heavy pose
+ *   sets but gives the same results) and one node-pair stack per warp, as many as fit.  A
+ *   pair of hierarchies whose stack bound leaves room for fewer than 4 warps would be
+ *   rejected with CBVH_ERR_WORKSPACE and a message giving the bytes needed; no pair this
+ *   library builds comes near that (the bound is at most 4,336 entries, 52 KB a warp).
  *   The pose count itself is not limited by the array.
  *   Set-up: the first call on a device looks up the array's device address (with that
  *   device current); make that first call before any stream capture.
@@ -253,6 +260,15 @@ int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_by
  *   larger; each bit costs one bit of lattice resolution.  Takes effect for builds started
  *   afterwards. */
 #define CBVH_OPT_LATTICE_HEADROOM 5
+/*   CBVH_OPT_WAIT_CAP: polls a bounded device wait makes before it gives up, 1..2^24
+ *   (default 2^24, about a minute with the wait's backoff).  It bounds the wait of an idle
+ *   warp for donated work in a work-queue launch and a block's first wait for its staged
+ *   treelets.  A wait that runs out sets `status` to CBVH_ERR_TIMEOUT and the kernel
+ *   returns; that query's results are then incomplete, and later queries are unaffected.
+ *   (Copies still in flight always get the full default wait before a block moves on.)
+ *   A small cap makes a query report CBVH_ERR_TIMEOUT on purpose, which is how failure
+ *   handling is tested.  Takes effect for queries issued afterwards. */
+#define CBVH_OPT_WAIT_CAP 6
 #define CBVH_PACK_TOP_DOWN 0
 #define CBVH_PACK_BOTTOM_UP 1
 int cbvh_set_option(int option, int64_t value);
@@ -343,6 +359,15 @@ int cbvh_profile_enable(int on);
  * traversal kernels of collide, 1 = those of distance (both of its passes), 2 = collide's
  * output compaction (scan, scatter, sort); then forgets them. */
 int cbvh_profile_collect(double *ms_host, int64_t *launches_host);
+
+/* Machine-ceiling probe: the L2 read bandwidth against which the traversal of hierarchies
+ * that stay in L2 is measured.  The paper has no counterpart.  Streams the caller's device
+ * `buffer` (`bytes` >= 16 KiB, a multiple of 16, 16-byte aligned; pick a size well inside
+ * L2) once to make it resident, then `reps` more times with 16-byte loads that bypass L1
+ * and are cached in L2 only, from every SM, timed with CUDA events on `stream` (the call
+ * synchronises).  gbs_host: bytes read / time, in GB/s.  sink: a device uint32 the kernel
+ * may write (keeps its loads live).  Errors: CBVH_ERR_ARG, CBVH_ERR_CUDA. */
+int cbvh_probe_l2_read(const void *buffer, int64_t bytes, int reps, uint32_t *sink, double *gbs_host, void *stream);
 
 #ifdef __cplusplus
 }

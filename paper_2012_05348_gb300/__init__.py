@@ -18,8 +18,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["BVH", "Batch", "collide", "distance", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
-           "set_option", "kernel_launches", "OPT_STAGE_BYTES", "OPT_LATTICE_HEADROOM", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
+__all__ = ["BVH", "Batch", "collide", "distance", "probe_l2_read", "workspace_bytes", "query_stats", "profile_enable", "profile_collect",
+           "set_option", "kernel_launches", "OPT_STAGE_BYTES", "OPT_LATTICE_HEADROOM", "OPT_WAIT_CAP", "WAIT_CAP_DEFAULT", "OPT_SPLIT", "OPT_BUDGET0", "OPT_TREELET_PACKING",
            "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "SPLIT_POSE", "SPLIT_ROUNDS", "SPLIT_QUEUE", "SPLIT_ROUNDS_QUEUE", "SPLIT_AUTO",
            "SPLIT_DEFAULT", "BUDGET0_DEFAULT", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
@@ -69,13 +69,14 @@ def _declare(L):
     L.cbvh_load.argtypes = [C.c_char_p, C.POINTER(P)]
     L.cbvh_build_device_workspace_bytes.argtypes = [P, C.POINTER(I64)]
     L.cbvh_build_device.argtypes = [P, P, P, P, I64, U32, P]
+    L.cbvh_probe_l2_read.argtypes = [P, I64, I32, P, P, P]
     for f in ("cbvh_build", "cbvh_free", "cbvh_info", "cbvh_blob_host", "cbvh_attach", "cbvh_decode_all",
               "cbvh_workspace_bytes", "cbvh_collide", "cbvh_distance", "cbvh_query_stats", "cbvh_profile_enable",
               "cbvh_profile_collect", "cbvh_distance_noalloc", "cbvh_batch_create", "cbvh_batch_free",
               "cbvh_batch_workspace_bytes", "cbvh_batch_upload", "cbvh_batch_launch", "cbvh_set_option",
               "cbvh_kernel_launches", "cbvh_refit_workspace_bytes", "cbvh_refit_prepare", "cbvh_refit",
               "cbvh_build_plan", "cbvh_build_device_workspace_bytes", "cbvh_build_device", "cbvh_save",
-              "cbvh_load"):
+              "cbvh_load", "cbvh_probe_l2_read"):
         getattr(L, f).restype = I32
     return L
 
@@ -281,6 +282,8 @@ OPT_SPLIT = 2
 OPT_BUDGET0 = 3
 OPT_TREELET_PACKING = 4
 OPT_LATTICE_HEADROOM = 5
+OPT_WAIT_CAP = 6
+WAIT_CAP_DEFAULT = 1 << 24
 PACK_TOP_DOWN, PACK_BOTTOM_UP = 0, 1
 # quant_bits values besides the delta widths 8 and 16
 QUANT_FP32, QUANT_FP16, QUANT_SVB = 0, 1, 2
@@ -299,8 +302,8 @@ def kernel_launches() -> int:
 
 
 def set_option(option: int, value: int) -> None:
-    """cbvh_set_option: process-wide tuning options (OPT_STAGE_BYTES, OPT_SPLIT, OPT_BUDGET0,
-    OPT_TREELET_PACKING)."""
+    """cbvh_set_option: process-wide options (OPT_STAGE_BYTES, OPT_SPLIT, OPT_BUDGET0,
+    OPT_TREELET_PACKING, OPT_LATTICE_HEADROOM, OPT_WAIT_CAP)."""
     _check(_load().cbvh_set_option(int(option), int(value)))
 
 
@@ -428,6 +431,17 @@ def profile_collect():
     _check(_load().cbvh_profile_collect(ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
     return {"collide": (float(ms[0]), int(n[0])), "distance": (float(ms[1]), int(n[1])),
             "compaction": (float(ms[2]), int(n[2]))}
+
+
+def probe_l2_read(nbytes: int = 64 << 20, reps: int = 20, device="cuda", stream=None) -> float:
+    """cbvh_probe_l2_read: L2 read bandwidth (GB/s) streaming an nbytes device buffer."""
+    torch = _torch()
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device=device)
+    sink = torch.zeros(1, dtype=torch.int32, device=device)
+    out = C.c_double()
+    with torch.cuda.device(buf.device):
+        _check(_load().cbvh_probe_l2_read(_ptr(buf), nbytes, reps, _ptr(sink), C.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def distance(A: BVH, B: BVH, poses, *, stream=None, check: bool = True):

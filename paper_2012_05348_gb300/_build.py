@@ -24,7 +24,7 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("build.cpp", "kernels.cu", "refit.cu", "devbuild.cu", "internal.h",
+    return [os.path.join(CSRC, f) for f in ("build.cpp", "kernels.cu", "refit.cu", "devbuild.cu", "probe.cu", "internal.h",
                                             "lattice.cuh")] + [
         os.path.join(INCLUDE, "cbvh.h")]
 
@@ -45,6 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     obj_dev = os.path.join(BUILD_DIR, "kernels.o")
     obj_refit = os.path.join(BUILD_DIR, "refit.o")
     obj_devbuild = os.path.join(BUILD_DIR, "devbuild.o")
+    obj_probe = os.path.join(BUILD_DIR, "probe.o")
     host_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-I", INCLUDE, "-c",
                 os.path.join(CSRC, "build.cpp"), "-o", obj_host]
     dev_cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -52,7 +53,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                "-o", obj_dev]
     refit_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "refit.cu"), "-o", obj_refit]
     devbuild_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "devbuild.cu"), "-o", obj_devbuild]
-    cmds = (host_cmd, dev_cmd, refit_cmd, devbuild_cmd)
+    probe_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "probe.cu"), "-o", obj_probe]
+    cmds = (host_cmd, dev_cmd, refit_cmd, devbuild_cmd, probe_cmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
     for p, c, o in zip(procs, cmds, outs):
@@ -61,7 +63,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and o:
             print(o)
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, obj_host, obj_dev, obj_refit, obj_devbuild]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, obj_host, obj_dev, obj_refit, obj_devbuild,
+            obj_probe]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")

@@ -81,7 +81,8 @@ struct Layout {
   int o_tagA, o_latA, o_pathA;
   int o_tagB, o_latB, o_pathB;
   int o_aset, o_bset, o_bvd, o_shift, o_abox;
-  int KS;  // row stride (floats) of the per-child direction arrays
+  int KS;      // row stride (floats) of the per-child direction arrays
+  int MA, MB;  // largest member set of A and of B (their branching factors): rows of the set arrays
 };
 
 // One work item of a batched query (see cbvh_batch_*): a pair of hierarchies, its poses and
@@ -127,6 +128,9 @@ struct Params {
   // queue_take); tasks_out is the queue and ready[i] != 0 once queue entry i is written
   int queue;
   uint32_t *ready;
+  // polls a waiting warp (work queue) or block (staged treelets) makes before it gives up
+  // and reports CBVH_ERR_TIMEOUT (CBVH_OPT_WAIT_CAP)
+  long long wait_cap;
   float invn[kMaxK];
   Layout L;
 };
@@ -661,7 +665,7 @@ __device__ bool stage_treelets(const Params &p, uint8_t *smem) {
   offsets(p.A, 0);
   offsets(p.B, 1);
   uint32_t done = 0;
-  for (long long i = 0; i < kStageSpin && !done; ++i)
+  for (long long i = 0; i < p.wait_cap && !done; ++i)
     asm volatile(
         "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
         : "=r"(done)
@@ -670,8 +674,9 @@ __device__ bool stage_treelets(const Params &p, uint8_t *smem) {
   const bool ok = __syncthreads_and(done) != 0;
   if (!ok) {
     if (threadIdx.x == 0) set_status(p.status, CBVH_ERR_TIMEOUT);
-    // the copies may still be in flight: give them a further bounded wait before the block
-    // goes on without them (their shared memory is never read)
+    // the copies may still be in flight: give them a further bounded wait of the full default
+    // length, whatever CBVH_OPT_WAIT_CAP says, before the block goes on without them (their
+    // shared memory is never read)
     for (long long i = 0; i < kStageSpin && !done; ++i)
       asm volatile(
           "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
@@ -696,8 +701,9 @@ __device__ bool stage_treelets(const Params &p, uint8_t *smem) {
 // ticket and waits for that slot's ready flag, so waiting warps poll different addresses;
 // tickets beyond the reserved slots tell donors how many warps are waiting.  Every pose
 // finished and no donated task unfinished means no slot can be filled any more: the warp
-// leaves.  A warp that waited kIdleSpin polls without either is reported as
-// CBVH_ERR_TIMEOUT (its slot could still be filled and would then be lost).
+// leaves.  A warp that waited p.wait_cap polls (CBVH_OPT_WAIT_CAP, default kIdleSpin)
+// without either is reported as CBVH_ERR_TIMEOUT (its slot could still be filled and would
+// then be lost).
 constexpr long long kIdleSpin = 1ll << 24;
 
 // Lane 0 of an idle warp: 1 and the task of its ticket, or 0 when all work is finished.
@@ -708,7 +714,7 @@ __device__ __noinline__ int queue_take(const Params &p, unsigned int *qc, uint32
   if (h >= p.task_cap) return 0;  // no slot can ever be reserved for this ticket
   volatile uint32_t *rd = p.ready;
   unsigned int nap = 64;
-  for (long long it = 0; it < kIdleSpin; ++it) {
+  for (long long it = 0; it < p.wait_cap; ++it) {
     if (rd[h]) {
       __threadfence();
       const volatile uint32_t *e = reinterpret_cast<const volatile uint32_t *>(p.tasks_out + h);
@@ -757,14 +763,15 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
           p.L.st_off[1],
           p.L.st_toff[1]};
   float2 *aiv = reinterpret_cast<float2 *>(ws + p.L.o_aset);  // A members' slabs (lo, hi) [i][KS]
-  uint32_t *aref = reinterpret_cast<uint32_t *>(aiv + kMaxM * KS);
-  uint32_t *aleaf = aref + kMaxM;
+  const int MA = p.L.MA, MB = p.L.MB;
+  uint32_t *aref = reinterpret_cast<uint32_t *>(aiv + MA * KS);
+  uint32_t *aleaf = aref + MA;
   float2 *bvv = reinterpret_cast<float2 *>(ws + p.L.o_bset);  // B members' axis slabs [i][0..2]
-  float4 *bcm = reinterpret_cast<float4 *>(bvv + kMaxM * 4);  // B members' box centre and M [i]
-  float4 *bhm = bcm + kMaxM;                                   // ... and half-size [i]
-  float2 *piv = reinterpret_cast<float2 *>(bhm + kMaxM);      // B members projected on A's directions [i][KS]
-  uint32_t *bref = reinterpret_cast<uint32_t *>(piv + kMaxM * KS);
-  uint32_t *bleaf = bref + kMaxM;
+  float4 *bcm = reinterpret_cast<float4 *>(bvv + MB * 4);  // B members' box centre and M [i]
+  float4 *bhm = bcm + MB;                                   // ... and half-size [i]
+  float2 *piv = reinterpret_cast<float2 *>(bhm + MB);      // B members projected on A's directions [i][KS]
+  uint32_t *bref = reinterpret_cast<uint32_t *>(piv + MB * KS);
+  uint32_t *bleaf = bref + MB;
   int *shift = reinterpret_cast<int *>(ws + p.L.o_shift);
   float2 *abox = reinterpret_cast<float2 *>(ws + p.L.o_abox);  // [i][3], valid while abox_ok
   bool abox_ok = false;
@@ -1479,14 +1486,20 @@ std::atomic<int> g_stage_bytes{kStageBytesDefault};
 std::atomic<int> g_split{4};  // work mapping, see launch_rounds
 std::atomic<long long> g_launches{0};  // kernels this library has launched (cbvh_kernel_launches)
 std::atomic<int> g_budget0{256};  // expansion budget of a task in round 0 (later rounds scale it)
+std::atomic<long long> g_wait_cap{kIdleSpin};  // polls of a bounded device wait (CBVH_OPT_WAIT_CAP)
 
 // Per-warp slice layout for A's direction count, the deepest nodes below a treelet root on
-// either side and a stack bound; no staged treelets.
-Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
+// either side, a stack bound and the largest branching factor on either side; no staged
+// treelets.  The set arrays are sized by the branching factors, not by the largest one
+// supported: shared memory taken from the SM's 256 KB is lost to L1, which caches the
+// stacks and the records.
+Layout warp_layout(int KA, int tdA, int tdB, int stack_cap, int mA, int mB) {
   Layout L;
   std::memset(&L, 0, sizeof L);
   L.tdA = tdA;
   L.tdB = tdB;
+  L.MA = mA;
+  L.MB = mB;
   L.KS = (KA & 1) ? KA : KA + 1;
   L.stack_cap = stack_cap;
   L.leafq_cap = 64;  // < 32 queued before a round of tests, a round adds <= 32
@@ -1511,15 +1524,15 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap) {
   L.o_pathB = o;
   o = align16(o + 4 * (tdB + 1));
   L.o_aset = o;
-  o = align16(o + 4 * (2 * kMaxM * L.KS + 2 * kMaxM));
+  o = align16(o + 4 * (2 * mA * L.KS + 2 * mA));
   L.o_bset = o;  // axis slabs (float2 x 4), box centre and half-size (float4 x 2), projections
-  o = align16(o + 4 * (2 * kMaxM * 4 + 8 * kMaxM + 2 * kMaxM * L.KS + 2 * kMaxM));
+  o = align16(o + 4 * (2 * mB * 4 + 8 * mB + 2 * mB * L.KS + 2 * mB));
   L.o_bvd = o;
   o = align16(o + 2 * (int)sizeof(BVd));
   L.o_shift = o;  // corrector shifts of the set being decoded, one per direction
   o = align16(o + 4 * kMaxK);
   L.o_abox = o;  // A members' axis boxes moved into B's frame, (lo, hi) per B axis
-  o = align16(o + 8 * 3 * kMaxM);
+  o = align16(o + 8 * 3 * mA);
   L.warp_bytes = o;
   return L;
 }
@@ -1532,7 +1545,7 @@ int64_t stack_stride(int stack_cap) { return ((int64_t)stack_cap * 12 + 15) & ~i
 int stack_bound(const cbvh_bvh *A, const cbvh_bvh *B) { return 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1); }
 
 Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
-  Layout L = warp_layout(A->K, A->max_tdepth, B->max_tdepth, stack_bound(A, B));
+  Layout L = warp_layout(A->K, A->max_tdepth, B->max_tdepth, stack_bound(A, B), A->m, B->m);
   // CTA region: the leading treelets of A and B that fit the staging budget
   int o = 0;
   const cbvh_bvh *H[2] = {A, B};
@@ -1670,9 +1683,12 @@ TraverseFn traverse_fn(int K, bool batch = false, bool var = false) {
 //      75.8 ms: every hand-off restarts decode chains), rounds are 3% faster for the
 //      early-exit arm sweep, and distances converge faster when rounds explore the
 //      subtrees a pose handed on side by side (sphere field 596 ms against 860 ms).
+// max_blocks: an upper bound on the grid (the allocation-free query has stacks for fewer
+// warps than the GPU holds).
 template <int MODE>
 int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint32_t *ready, uint2 *stacks,
-                  uint32_t task_cap, int sms, cudaStream_t s, int slot = MODE, bool early_all = false) {
+                  uint32_t task_cap, int sms, cudaStream_t s, int slot = MODE, bool early_all = false,
+                  int64_t max_blocks = INT32_MAX) {
   const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
   const TraverseFn fn =
       traverse_fn<MODE>(p.A.K, p.items != nullptr, p.A.bits == CBVH_QUANT_SVB || p.B.bits == CBVH_QUANT_SVB);
@@ -1683,7 +1699,7 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint32
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
   per_sm = std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock);
-  const int blocks = sms * per_sm;
+  const int blocks = (int)std::min<int64_t>((int64_t)sms * per_sm, max_blocks);
   uint4 *buf[2] = {buf0, buf1};
   p.stacks = stacks;
   p.task_cap = task_cap;
@@ -1757,6 +1773,7 @@ void fill_params(Params &p, const cbvh_bvh *A, const cbvh_bvh *B) {
   p.A = view(A);
   p.B = view(B);
   p.L = make_layout(A, B);
+  p.wait_cap = g_wait_cap.load();
   for (int j = 0; j < kMaxK; ++j) {
     static const int n2[kMaxK] = {1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3};
     float f = (float)(1.0 / std::sqrt((double)n2[j]));
@@ -1960,11 +1977,13 @@ extern "C" int cbvh_profile_collect(double *ms_host, int64_t *launches_host) {
 }
 
 // ---------------------------------------------------------------- distance without allocation
-// Scratch of cbvh_distance_noalloc: counters, the two task buffers and the per-warp stacks
-// of the proximity query, in one fixed array that every GPU loading this library holds
-// until the process exits.  Calls share it, so calls that overlap on the GPU race.
+// Scratch of cbvh_distance_noalloc, in one fixed array that every GPU loading this library
+// holds until the process exits: the counters of both passes, the intersection flags of one
+// chunk of poses, the two task buffers with the ready flags of a work-queue round, and the
+// per-warp stacks.  Calls share it, so calls that overlap on the GPU race.
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
 constexpr uint32_t kNoAllocTasks = 1u << 17;               // entries per task buffer
+constexpr int64_t kNoAllocChunk = int64_t(1) << 20;        // poses per chunk (one flag byte each)
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
@@ -2001,56 +2020,56 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
   if (int rc = device_sms(&sms)) return rc;
   Params p;
   fill_params(p, A, B);
-  // carve the fixed array: counters, two task buffers, then as many warp stacks as fit
-  const int64_t tasks_bytes = 16 * (int64_t)kNoAllocTasks;
-  const int64_t stacks_off = kWsHeader + 2 * tasks_bytes;
+  // carve the fixed array: counters, the chunk's flags, two task buffers, the ready flags,
+  // then as many warp stacks as fit
+  const int64_t o_flags = kWsHeader;
+  const int64_t o_tasks0 = align256(o_flags + kNoAllocChunk);
+  const int64_t o_tasks1 = align256(o_tasks0 + 16 * (int64_t)kNoAllocTasks);
+  const int64_t o_ready = align256(o_tasks1 + 16 * (int64_t)kNoAllocTasks);
+  const int64_t o_stacks = align256(o_ready + 4 * (int64_t)kNoAllocTasks);
   const int64_t per_warp = stack_stride(p.L.stack_cap);
-  const int64_t warps_fit = ((int64_t)kNoAllocScratchBytes - stacks_off) / per_warp;
+  const int64_t warps_fit = ((int64_t)kNoAllocScratchBytes - o_stacks) / per_warp;
   if (warps_fit < kWarpsPerBlock)
     return cbvh::fail(CBVH_ERR_WORKSPACE,
-                      "this pair of hierarchies needs " + std::to_string(per_warp * kWarpsPerBlock + stacks_off) +
+                      "this pair of hierarchies needs " + std::to_string(per_warp * kWarpsPerBlock + o_stacks) +
                           " bytes of scratch; cbvh_distance_noalloc has " + std::to_string(kNoAllocScratchBytes));
-  const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
-  const TraverseFn fn = traverse_fn<MODE_PQ>(p.A.K, false, p.A.bits == CBVH_QUANT_SVB || p.B.bits == CBVH_QUANT_SVB);
-  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
-  if (per_sm < 1) return cbvh::fail(CBVH_ERR_ARG, "traversal state does not fit in shared memory");
-  const int blocks = (int)std::min<int64_t>((int64_t)sms * std::min(per_sm, kMaxWarpsPerSM / kWarpsPerBlock),
-                                            warps_fit / kWarpsPerBlock);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint8_t *ws = static_cast<uint8_t *>(scratch);
-  // the counters must start at zero; the task buffers and stacks are written before read
-  e = cudaMemsetAsync(ws, 0, kWsHeader, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  if (n == 0) return CBVH_OK;
-  p.poses = poses;
-  p.n = n;
-  p.dist = dist;
-  p.status = status;
-  p.stats = reinterpret_cast<unsigned long long *>(ws + 16);
-  p.stacks = reinterpret_cast<uint2 *>(ws + stacks_off);
-  p.task_cap = kNoAllocTasks;
-  unsigned int *next = reinterpret_cast<unsigned int *>(ws + 64);
-  unsigned int *count = reinterpret_cast<unsigned int *>(ws + 128);
-  uint4 *buf[2] = {reinterpret_cast<uint4 *>(ws + kWsHeader), reinterpret_cast<uint4 *>(ws + kWsHeader + tasks_bytes)};
-  for (int r = 0; r < kRounds; ++r) {
-    p.round = r;
-    p.last_round = r == kRounds - 1;
-    p.budget = kBudget[r];
-    p.task_next = next + r;
-    p.count_in = count + r;
-    p.count_out = count + r + 1;
-    p.tasks_in = buf[(r + 1) & 1];
-    p.tasks_out = buf[r & 1];
-    fn<<<blocks, kThreads, smem, s>>>(p);
-    g_launches.fetch_add(1);
+  uint4 *t0 = reinterpret_cast<uint4 *>(ws + o_tasks0), *t1 = reinterpret_cast<uint4 *>(ws + o_tasks1);
+  uint32_t *rdy = reinterpret_cast<uint32_t *>(ws + o_ready);
+  uint2 *st = reinterpret_cast<uint2 *>(ws + o_stacks);
+  const int64_t max_blocks = warps_fit / kWarpsPerBlock;
+  // the two passes of cbvh_distance with its schedule, chunk by chunk
+  for (int64_t off = 0; off < n; off += kNoAllocChunk) {
+    const int64_t cnt = std::min(kNoAllocChunk, n - off);
+    // the counters of both passes must start at zero; everything else is written before read
+    e = cudaMemsetAsync(ws, 0, kWsHeader, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    Params q = p;
+    q.poses = poses + 12 * off;
+    q.n = cnt;
+    q.hit = ws + o_flags;
+    q.flags = CBVH_EARLY_EXIT;
+    q.status = status;
+    q.pair_count = reinterpret_cast<unsigned long long *>(ws);
+    q.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+    if (int rc = launch_rounds<MODE_CD>(q, reinterpret_cast<unsigned int *>(ws + 64), t0, t1, rdy, st, kNoAllocTasks,
+                                        sms, s, 1, true, max_blocks))
+      return rc;
+    Params r = p;
+    r.poses = poses + 12 * off;
+    r.n = cnt;
+    r.dist = dist + off;
+    r.status = status;
+    r.skip = ws + o_flags;
+    r.stats = reinterpret_cast<unsigned long long *>(ws + 16);
+    if (int rc = launch_rounds<MODE_PQ>(r, reinterpret_cast<unsigned int *>(ws + 160), t0, t1, rdy, st, kNoAllocTasks,
+                                        sms, s, MODE_PQ, false, max_blocks))
+      return rc;
   }
-  e = cudaGetLastError();
-  return e == cudaSuccess ? CBVH_OK : cuda_fail(e, "traverse launch");
+  return CBVH_OK;
 }
 
 // ---------------------------------------------------------------- batched queries
@@ -2109,7 +2128,7 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
       g.first = (int)b->items.size();
       g.count = (int)idx.size();
       g.bases_at = (int64_t)b->bases.size();
-      int tdA = 0, tdB = 0, sc = 1;
+      int tdA = 0, tdB = 0, sc = 1, mA = 2, mB = 2;
       unsigned long long acc = 0;
       for (int64_t i : idx) {
         const cbvh_query_t &x = q[i];
@@ -2127,10 +2146,12 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
         tdA = std::max(tdA, x.A->max_tdepth);
         tdB = std::max(tdB, x.B->max_tdepth);
         sc = std::max(sc, stack_bound(x.A, x.B));
+        mA = std::max(mA, x.A->m);
+        mB = std::max(mB, x.B->m);
       }
       b->bases.push_back(acc);
       g.poses = (int64_t)acc;
-      g.L = warp_layout(K, tdA, tdB, sc);
+      g.L = warp_layout(K, tdA, tdB, sc, mA, mB);
       g.A0 = view(q[idx[0]].A);
       g.B0 = view(q[idx[0]].B);
       g.pre_first = -1;
@@ -2234,6 +2255,7 @@ extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t w
     p.A = g.A0;
     p.B = g.B0;
     p.L = g.L;
+    p.wait_cap = g_wait_cap.load();
     for (int j = 0; j < kMaxK; ++j) {
       static const int n2[kMaxK] = {1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3};
       float f = (float)(1.0 / std::sqrt((double)n2[j]));
@@ -2293,6 +2315,11 @@ extern "C" int cbvh_set_option(int option, int64_t value) {
   if (option == CBVH_OPT_SPLIT) {
     if (value < 0 || value > 4) return cbvh::fail(CBVH_ERR_ARG, "split must be 0, 1, 2, 3 or 4");
     g_split.store((int)value);
+    return CBVH_OK;
+  }
+  if (option == CBVH_OPT_WAIT_CAP) {
+    if (value < 1 || value > kIdleSpin) return cbvh::fail(CBVH_ERR_ARG, "wait cap must be in [1, 2^24] polls");
+    g_wait_cap.store(value);
     return CBVH_OK;
   }
   if (option == CBVH_OPT_LATTICE_HEADROOM) {

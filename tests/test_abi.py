@@ -134,6 +134,10 @@ def test_batch_rejects_unattached_handles(cb):
     assert cb.lib.cbvh_set_option(cb.OPT_STAGE_BYTES, 1 << 20) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_TREELET_PACKING, 2) == -1
     assert cb.lib.cbvh_set_option(cb.OPT_SPLIT, 5) == -1
+    assert cb.lib.cbvh_set_option(cb.OPT_WAIT_CAP, 0) == -1
+    assert cb.lib.cbvh_set_option(cb.OPT_WAIT_CAP, (1 << 24) + 1) == -1
+    assert cb.lib.cbvh_set_option(cb.OPT_WAIT_CAP, cb.WAIT_CAP_DEFAULT) == 0
+    assert cb.lib.cbvh_probe_l2_read(None, 1 << 20, 1, None, None, None) == -1
 
 
 def test_kernel_launch_counter_without_gpu(cb):

@@ -43,6 +43,48 @@ def _noalloc(cb, A, B, P):
     return dist.cpu().numpy()
 
 
+def test_distance_noalloc_matches_the_oracle_on_two_calls(cb):
+    """The small sphere pair (1,280 triangles each, 256 poses away from contact) against the
+    FP64 oracle: within 1e-5 of the scene diameter, zero exactly where the oracle's is."""
+    import torch
+    import oracle
+    c = synth.C1(4)
+    (va, ta), (vb, tb) = c["A"], c["B"]
+    Ao = oracle.BVH(va, ta, 18, 4, 16, 4096)
+    Bo = oracle.BVH(vb, tb, 18, 4, 16, 4096)
+    D = synth.scene_diameter(va, vb)
+    P = oracle.filtered_poses(Ao, Bo, lambda cnt, r: synth.poses_box(cnt, seed=2001 + 7919 * r), 256, 1e-6 * D)
+    o_d, _ = oracle.distance(Ao, Bo, P)
+    A = cb.BVH(va, ta, 18, 4, 16, 4096)
+    B = cb.BVH(vb, tb, 18, 4, 16, 4096)
+    Pd = torch.as_tensor(P, device="cuda")
+    for _ in range(2):
+        got = _noalloc(cb, A, B, Pd).astype(np.float64)
+        assert np.abs(got - o_d).max() <= TOL_PQ * D
+        assert ((got == 0) == (o_d == 0)).all()
+    assert (o_d == 0).sum() > 20 and (o_d > 0).sum() > 20
+
+
+def test_distance_noalloc_sequence_of_different_pairs(cb):
+    """Spheres, then the terrain at the full 10,000 poses (enough handed-on work to fill the
+    fixed task buffers), then the spheres again: each call equals cbvh_distance, whatever
+    the previous call left in the shared array."""
+    import torch
+    s = synth.C1(300)
+    t = synth.C2(10000)
+    cases = []
+    for c, cfg in ((s, (18, 4, 16, 4096)), (t, (24, 8, 8, 16384))):
+        (va, ta), (vb, tb) = c["A"], c["B"]
+        A, B = cb.BVH(va, ta, *cfg), cb.BVH(vb, tb, *cfg)
+        P = torch.as_tensor(c["poses"], device="cuda")
+        cases.append((A, B, P, synth.scene_diameter(va, vb), cb.distance(A, B, P).cpu().numpy()))
+    for k in (0, 1, 0):
+        A, B, P, D, ref = cases[k]
+        got = _noalloc(cb, A, B, P)
+        assert np.abs(got - ref).max() <= TOL_PQ * D
+        assert ((got == 0) == (ref == 0)).all()
+
+
 @pytest.mark.parametrize("case", ["spheres", "terrain"])
 def test_distance_noalloc_matches_distance_on_two_calls(cb, case):
     import torch
