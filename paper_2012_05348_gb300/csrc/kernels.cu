@@ -82,7 +82,8 @@ struct Layout {
   int o_tagB, o_latB, o_pathB;
   int o_aset, o_bset, o_bvd, o_shift, o_abox;
   int KS;      // row stride (floats) of the per-child direction arrays
-  int MA, MB;  // largest member set of A and of B (their branching factors): rows of the set arrays
+  int MA, MB;  // rows of A's and of B's set arrays: E x A's branching factor, B's branching factor
+  int E;       // node pairs expanded together (see the pop in traverse_kernel), E x mA <= kMaxM
 };
 
 // One work item of a batched query (see cbvh_batch_*): a pair of hierarchies, its poses and
@@ -318,7 +319,7 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, con
 // written to iv (row stride KS), references to ref[], and leaf slots (or 0xffffffff) to
 // leaf[].  Returns
 // the number of members (warp-uniform).
-template <int ND, bool VAR>
+template <int ND, bool VAR, bool LAT>
 __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float2 *iv, int KS,
                           uint32_t *ref, uint32_t *leaf, int *shift, bool leaf_bounds = true) {
   const uint32_t t = x >> X.lbits;
@@ -340,7 +341,7 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     __syncwarp();
     return 1;
   }
-  if (X.bits <= 1) {  // absolute bounds in every record
+  if (!LAT && X.bits <= 1) {  // absolute bounds in every record
     if (self) {
       if (lane < nd) iv[lane] = abs_bound(rx, lane, X.bits);
       if (lane == 0) {
@@ -729,7 +730,104 @@ __device__ __noinline__ int queue_take(const Params &p, unsigned int *qc, uint32
   return 0;
 }
 
-template <int MODE, int KA, bool BATCH, bool VAR>
+// Work donation (work queue): a busy warp gives as many entries from the bottom of its stack
+// -- its shallowest, largest subtrees -- as warps wait beyond the reserved slots, at most
+// half its stack, and keeps the rest.  Returns the new stack size.  Kept out of line: it runs
+// at most every 64 expansions, and the traversal's loop must stay small enough for the
+// instruction cache.
+template <int MODE>
+__device__ __noinline__ int donate(const Params &p, unsigned int *qc, uint2 *stack, float *stack_lb, int sp,
+                                   uint32_t gid, int lane) {
+  int want = 0;
+  if (lane == 0) {
+    const int waiting = (int)(*reinterpret_cast<volatile unsigned int *>(&qc[1]) -
+                              *reinterpret_cast<volatile unsigned int *>(&qc[2]));
+    want = min(waiting, sp >> 1);
+  }
+  want = __shfl_sync(kFull, want, 0);
+  if (want <= 0) return sp;
+  uint32_t base = 0;
+  int ok = 0;
+  if (lane == 0) {
+    atomicAdd(&qc[3], (unsigned int)want);  // counted before the slots exist
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(&qc[2]);
+    for (int tries = 0; tries < 64; ++tries) {
+      if ((unsigned long long)old + want > p.task_cap) break;
+      const uint32_t prev = atomicCAS(&qc[2], old, old + (uint32_t)want);
+      if (prev == old) {
+        ok = 1;
+        base = old;
+        break;
+      }
+      old = prev;
+    }
+    if (!ok) atomicSub(&qc[3], (unsigned int)want);
+    __threadfence();
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  base = __shfl_sync(kFull, base, 0);
+  if (!ok) return sp;
+  // (handing out the entries just below the top instead made PQ several times slower: the
+  // pieces are small and the donor runs dry)
+  for (int k = lane; k < want; k += 32) {
+    const uint2 e = stack[k];
+    p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, MODE == MODE_PQ ? __float_as_uint(stack_lb[k]) : 0u);
+    __threadfence();
+    *reinterpret_cast<volatile uint32_t *>(&p.ready[base + k]) = 1u;
+  }
+  for (int i0 = 0; i0 < sp - want; i0 += 32) {
+    const bool in = i0 + lane < sp - want;
+    uint2 e = make_uint2(0u, 0u);
+    float l = 0.f;
+    if (in) {
+      e = stack[want + i0 + lane];
+      if (MODE == MODE_PQ) l = stack_lb[want + i0 + lane];
+    }
+    __syncwarp();
+    if (in) {
+      stack[i0 + lane] = e;
+      if (MODE == MODE_PQ) stack_lb[i0 + lane] = l;
+    }
+    __syncwarp();
+  }
+  return sp - want;
+}
+
+// Rounds: a task over its expansion budget moves its whole stack into the next round's task
+// buffer.  Returns whether it did (false: the buffer is full and the warp keeps the work).
+template <int MODE>
+__device__ __noinline__ bool hand_on(const Params &p, const uint2 *stack, const float *stack_lb, int sp, uint32_t gid,
+                                     int lane) {
+  uint32_t base = 0;
+  int ok = 0;
+  if (lane == 0) {
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(p.count_out);
+    for (int tries = 0; tries < 64; ++tries) {
+      if ((unsigned long long)old + sp > p.task_cap) break;
+      const uint32_t prev = atomicCAS(p.count_out, old, old + (uint32_t)sp);
+      if (prev == old) {
+        ok = 1;
+        base = old;
+        break;
+      }
+      old = prev;
+    }
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  base = __shfl_sync(kFull, base, 0);
+  if (!ok) return false;
+  for (int k = lane; k < sp; k += 32) {
+    const uint2 e = stack[k];
+    p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, MODE == MODE_PQ ? __float_as_uint(stack_lb[k]) : 0u);
+  }
+  __syncwarp();
+  return true;
+}
+
+// LAT: both hierarchies store predictor-corrector deltas (8 or 16 bits); the kernel then
+// carries no decode path for absolute bounds, which keeps its loop small for the
+// instruction cache.
+template <int MODE, int KA, bool BATCH, bool VAR, bool LAT>
 __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traverse_kernel(const Params p) {
   uint8_t *smem = g_dsmem;
   const int lane = threadIdx.x & 31;
@@ -951,6 +1049,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
     uint32_t nhits = 0;
     bool done = false;
     int expansions = 0;
+    int nx = 0;                         // further node pairs (ax[q], b) expanded with (a, b)
+    uint32_t ax0 = 0, ax1 = 0, ax2 = 0;
     // checkPrimitives on the last `cnt` queued leaf pairs, one pair per lane
     auto drain = [&](int cnt) {
       nleaf -= cnt;
@@ -1005,17 +1105,25 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       // ---------------- expand (a, b) as Algorithm 1 does ----------------
       // A's member set depends on a only, B's projected set on b and the pose: in depth-first
       // order one of them is often the same as in the previous expansion and is reused.
+      // Several popped pairs (a, b), (ax0, b), ... that share b expand as one: the member
+      // sets of their A nodes are decoded one after another into consecutive rows, and their
+      // pairs with B's members tested, compacted and pushed together, which fills the lanes
+      // of the pair loop and shares the expansion's fixed costs.
       int na, nb;
-      if (a != keyA || root) {
-        na = decode_set<KA, VAR>(A, SA, a, root, lane, aiv, KS, aref, aleaf, shift);
-        keyA = root ? 0xffffffffu : a;
+      if (nx > 0 || a != keyA || root) {
+        na = 0;
+        for (int q = 0; q <= nx; ++q) {
+          const uint32_t x = q == 0 ? a : (q == 1 ? ax0 : (q == 2 ? ax1 : ax2));
+          na += decode_set<KA, VAR, LAT>(A, SA, x, root, lane, aiv + na * KS, KS, aref + na, aleaf + na, shift);
+        }
+        keyA = (root || nx > 0) ? 0xffffffffu : a;
         na_c = na;
         abox_ok = false;
       } else {
         na = na_c;
       }
       if (b != keyB || root) {
-        nb = decode_set<3, VAR>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
+        nb = decode_set<3, VAR, LAT>(B, SB, b, root, lane, bvv, 4, bref, bleaf, shift, false);
         if (lane < nb && bleaf[lane] == 0xffffffffu) member_box(bvv, lane, bcm[lane], bhm[lane]);
         if (lane < 3 * nb) {  // leaf members: the exact box of their triangle
           const int i = lane / 3, x = lane - 3 * i;
@@ -1038,7 +1146,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       }
       root = false;
       ++expansions;
-      ++n_exp;
+      n_exp += 1 + nx;
       // test every member pair; survivors are compacted by ballot onto the stack (inner
       // pairs) or the leaf queue (leaf pairs)
       if (!abox_ok) {
@@ -1157,9 +1265,6 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         nleaf += __popc(ml);
         sp += __popc(mi);
         __syncwarp();
-        while (nleaf >= 32 && !done) drain(32);
-        // PQ: until some distance is known nothing can be pruned, so test leaf pairs at once
-        if (MODE == MODE_PQ && nleaf > 0 && best == INFINITY && !done) drain(nleaf);
       }
       // PQ: the most promising child pair goes on top, so that it is expanded next
       if (MODE == MODE_PQ && run_pos >= 0 && run_pos != sp - 1 && !done) {
@@ -1173,120 +1278,71 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         }
         __syncwarp();
       }
-      if (done || sp == 0) break;
-      // ---------------- donate the bottom of the stack to waiting warps ----------------
-      // (checked every 64 expansions: the check reads two global counters)
-      if (p.queue && sp >= 2 && expansions >= p.budget && (expansions & 63) == 0) {
-        int want = 0;
-        if (lane == 0) {
-          const int waiting = (int)(*reinterpret_cast<volatile unsigned int *>(&qc[1]) -
-                                    *reinterpret_cast<volatile unsigned int *>(&qc[2]));
-          want = min(waiting, sp >> 1);
-        }
-        want = __shfl_sync(kFull, want, 0);
-        if (want > 0) {
-          uint32_t base = 0;
-          int ok = 0;
-          if (lane == 0) {
-            atomicAdd(&qc[3], (unsigned int)want);  // counted before the slots exist
-            uint32_t old = *reinterpret_cast<volatile uint32_t *>(&qc[2]);
-            for (int tries = 0; tries < 64; ++tries) {
-              if ((unsigned long long)old + want > p.task_cap) break;
-              const uint32_t prev = atomicCAS(&qc[2], old, old + (uint32_t)want);
-              if (prev == old) {
-                ok = 1;
-                base = old;
-                break;
-              }
-              old = prev;
-            }
-            if (!ok) atomicSub(&qc[3], (unsigned int)want);
-            __threadfence();
-          }
-          ok = __shfl_sync(kFull, ok, 0);
-          base = __shfl_sync(kFull, base, 0);
-          if (ok) {
-            // the bottom entries are the shallowest, largest subtrees (handing out the
-            // entries just below the top instead made PQ several times slower: the pieces
-            // are small and the donor runs dry)
-            for (int k = lane; k < want; k += 32) {
-              const uint2 e = stack[k];
-              p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, MODE == MODE_PQ ? __float_as_uint(stack_lb[k]) : 0u);
-              __threadfence();
-              *reinterpret_cast<volatile uint32_t *>(&p.ready[base + k]) = 1u;
-            }
-            for (int i0 = 0; i0 < sp - want; i0 += 32) {
-              const bool in = i0 + lane < sp - want;
-              uint2 e = make_uint2(0u, 0u);
-              float l = 0.f;
-              if (in) {
-                e = stack[want + i0 + lane];
-                if (MODE == MODE_PQ) l = stack_lb[want + i0 + lane];
-              }
-              __syncwarp();
-              if (in) {
-                stack[i0 + lane] = e;
-                if (MODE == MODE_PQ) stack_lb[i0 + lane] = l;
-              }
-              __syncwarp();
-            }
-            sp -= want;
-          }
-        }
-      }
-      // ---------------- hand the rest of this task on ----------------
-      if (!p.queue && may_spill && expansions >= p.budget && sp >= 2) {
-        uint32_t base = 0;
-        int ok = 0;
-        if (lane == 0) {
-          uint32_t old = *reinterpret_cast<volatile uint32_t *>(p.count_out);
-          for (int tries = 0; tries < 64; ++tries) {
-            if ((unsigned long long)old + sp > p.task_cap) break;
-            const uint32_t prev = atomicCAS(p.count_out, old, old + (uint32_t)sp);
-            if (prev == old) {
-              ok = 1;
-              base = old;
-              break;
-            }
-            old = prev;
-          }
-        }
-        ok = __shfl_sync(kFull, ok, 0);
-        base = __shfl_sync(kFull, base, 0);
-        if (ok) {
-          for (int k = lane; k < sp; k += 32) {
-            const uint2 e = stack[k];
-            p.tasks_out[base + k] = make_uint4(gid, e.x, e.y, MODE == MODE_PQ ? __float_as_uint(stack_lb[k]) : 0u);
-          }
+      // ---------------- leaf tests, scheduling ----------------
+      // Leaf pairs are tested (checkPrimitives) 32 at a time: full batches; everything once
+      // the task stops (no node pairs left, or the rest handed on); and for PQ everything
+      // while no distance is known, since until then nothing can be pruned.  Between the
+      // batches and the pop: donation to waiting warps, hand-off to the next round, the
+      // periodic poll of the pose's shared result, and (PQ) dropping stale entries.  The
+      // loop below is the one place the triangle tests are compiled in.
+      bool stop = done || sp == 0;
+      for (bool first = true;; first = false) {
+        while (!done && nleaf > 0 && (nleaf >= 32 || stop || (MODE == MODE_PQ && best == INFINITY)))
+          drain(min(nleaf, 32));
+        if (done || stop || !first) break;
+        if (p.queue && sp >= 2 && expansions >= p.budget && (expansions & 63) == 0)
+          sp = donate<MODE>(p, qc, stack, stack_lb, sp, gid, lane);
+        if (!p.queue && may_spill && expansions >= p.budget && sp >= 2 && hand_on<MODE>(p, stack, stack_lb, sp, gid, lane)) {
           sp = 0;
-          __syncwarp();
-          break;
+          stop = true;
         }
-      }
-      if ((expansions & (early ? 3 : 15)) == 0) {
-        if (MODE == MODE_PQ) {
-          float v = 0.f;
-          if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
-          best = fminf(best, __shfl_sync(kFull, v, 0));
-        } else if (early) {
-          int h = 0;
-          if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
-          if (__shfl_sync(kFull, h, 0)) break;
+        if (!stop && (expansions & (early ? 3 : 15)) == 0) {
+          if (MODE == MODE_PQ) {
+            float v = 0.f;
+            if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
+            best = fminf(best, __shfl_sync(kFull, v, 0));
+          } else if (early) {
+            int h = 0;
+            if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
+            if (__shfl_sync(kFull, h, 0)) done = true;  // another task of the pose found a pair
+          }
         }
+        // PQ: entries whose lower bound reached the best distance found since they were
+        // pushed cannot hold a closer pair and are dropped
+        if (MODE == MODE_PQ && !stop) {
+          while (sp > 0 && stack_lb[sp - 1] >= best) --sp;
+          if (sp == 0) stop = true;
+        }
+        if (!stop) break;
       }
+      if (done || stop) break;
       // ---------------- pop ----------------
-      // PQ: entries whose lower bound reached the best distance found since they were
-      // pushed cannot hold a closer pair and are dropped
-      if (MODE == MODE_PQ) {
-        while (sp > 0 && stack_lb[sp - 1] >= best) --sp;
-        if (sp == 0) break;
-      }
+      // the top pair, and up to E - 1 more below it with the same B node (pairs are pushed
+      // B-major, so the children of one expansion with one B member lie together on top)
       const uint2 e = stack[--sp];
       a = e.x;
       b = e.y;
+      nx = 0;
+      if (p.L.E > 1) {
+        bool more = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (more && q < p.L.E - 1 && sp > 0) {
+            const uint2 f = stack[sp - 1];
+            if (f.y == b && (MODE == MODE_CD || stack_lb[sp - 1] < best)) {
+              if (q == 0) ax0 = f.x;
+              if (q == 1) ax1 = f.x;
+              if (q == 2) ax2 = f.x;
+              --sp;
+              ++nx;
+            } else {
+              more = false;
+            }
+          }
+        }
+      }
       __syncwarp();
     }
-    while (!done && nleaf > 0) drain(min(nleaf, 32));
     nleaf = 0;
     if (lane == 0) {
       if (MODE == MODE_CD) {
@@ -1502,7 +1558,7 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap, int mA, int mB) {
   L.MB = mB;
   L.KS = (KA & 1) ? KA : KA + 1;
   L.stack_cap = stack_cap;
-  L.leafq_cap = 64;  // < 32 queued before a round of tests, a round adds <= 32
+  L.leafq_cap = 32 + mA * mB;  // < 32 queued before an expansion, which adds <= mA mB
   int o = 0;
   L.o_stack = -1;  // stacks live in global memory
   L.o_leafq = o;
@@ -1542,10 +1598,21 @@ Layout warp_layout(int KA, int tdA, int tdB, int stack_cap, int mA, int mB) {
 int64_t stack_stride(int stack_cap) { return ((int64_t)stack_cap * 12 + 15) & ~int64_t(15); }
 
 // Stack bound: every level of the node-pair tree leaves at most (mA mB - 1) siblings.
-int stack_bound(const cbvh_bvh *A, const cbvh_bvh *B) { return 1 + (A->depth + B->depth + 1) * (A->m * B->m - 1); }
+// Pairs expanded together: as many A member sets as fill kMaxM rows, at most 4.
+int joint_pairs(int mA) { return std::max(1, std::min(4, kMaxM / mA)); }
+// Stack bound: every level of the node-pair tree leaves at most (E mA mB - 1) siblings, E
+// pairs being expanded together.
+int stack_bound(const cbvh_bvh *A, const cbvh_bvh *B, int E) {
+  return 1 + (A->depth + B->depth + 1) * (E * A->m * B->m - 1);
+}
 
-Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B) {
-  Layout L = warp_layout(A->K, A->max_tdepth, B->max_tdepth, stack_bound(A, B), A->m, B->m);
+// mode 0: collision detection (node pairs sharing a B node expanded together); 1: proximity
+// query (one pair at a time: its most promising pair goes on top of the stack and is
+// expanded next, which joint expansion would dilute -- measured slower on the terrain).
+Layout make_layout(const cbvh_bvh *A, const cbvh_bvh *B, int mode) {
+  const int E = mode == 0 ? joint_pairs(A->m) : 1;
+  Layout L = warp_layout(A->K, A->max_tdepth, B->max_tdepth, stack_bound(A, B, E), E * A->m, B->m);
+  L.E = E;
   // CTA region: the leading treelets of A and B that fit the staging budget
   int o = 0;
   const cbvh_bvh *H[2] = {A, B};
@@ -1650,21 +1717,24 @@ int device_sms(int *sms) {
 
 // The traversal kernel compiled for A's number of slab directions (k = 6, 18, 24, 26).
 typedef void (*TraverseFn)(const Params);
-// var: a Stream VByte hierarchy takes part (single queries only; batches refuse them).
-template <int MODE, bool BATCH, bool VAR>
+// var: a Stream VByte hierarchy takes part (single queries only; batches refuse them);
+// lat: both hierarchies store 8- or 16-bit deltas (single queries).
+template <int MODE, bool BATCH, bool VAR, bool LAT>
 TraverseFn traverse_fn_b(int K) {
   switch (K) {
-    case 3: return traverse_kernel<MODE, 3, BATCH, VAR>;
-    case 9: return traverse_kernel<MODE, 9, BATCH, VAR>;
-    case 12: return traverse_kernel<MODE, 12, BATCH, VAR>;
-    default: return traverse_kernel<MODE, 13, BATCH, VAR>;
+    case 3: return traverse_kernel<MODE, 3, BATCH, VAR, LAT>;
+    case 9: return traverse_kernel<MODE, 9, BATCH, VAR, LAT>;
+    case 12: return traverse_kernel<MODE, 12, BATCH, VAR, LAT>;
+    default: return traverse_kernel<MODE, 13, BATCH, VAR, LAT>;
   }
 }
 template <int MODE>
-TraverseFn traverse_fn(int K, bool batch = false, bool var = false) {
-  if (batch) return traverse_fn_b<MODE, true, false>(K);
-  return var ? traverse_fn_b<MODE, false, true>(K) : traverse_fn_b<MODE, false, false>(K);
+TraverseFn traverse_fn(int K, bool batch, bool var, bool lat) {
+  if (batch) return traverse_fn_b<MODE, true, false, false>(K);
+  if (var) return traverse_fn_b<MODE, false, true, false>(K);
+  return lat ? traverse_fn_b<MODE, false, false, true>(K) : traverse_fn_b<MODE, false, false, false>(K);
 }
+bool delta_bits(int bits) { return bits == 8 || bits == 16; }
 
 // Launches one traversal pass.  ctr: 24 zeroed u32 counters -- [0, 8) the task cursor of
 // each round, [8, 16) the task count of each round, [16, 24) the work-queue counters; buf:
@@ -1691,7 +1761,8 @@ int launch_rounds(Params &p, unsigned int *ctr, uint4 *buf0, uint4 *buf1, uint32
                   int64_t max_blocks = INT32_MAX) {
   const int smem = p.L.cta_bytes + kWarpsPerBlock * p.L.warp_bytes;
   const TraverseFn fn =
-      traverse_fn<MODE>(p.A.K, p.items != nullptr, p.A.bits == CBVH_QUANT_SVB || p.B.bits == CBVH_QUANT_SVB);
+      traverse_fn<MODE>(p.A.K, p.items != nullptr, p.A.bits == CBVH_QUANT_SVB || p.B.bits == CBVH_QUANT_SVB,
+                        delta_bits(p.A.bits) && delta_bits(p.B.bits));
   cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int per_sm = 0;
@@ -1768,11 +1839,11 @@ int check_pair(const cbvh_bvh *A, const cbvh_bvh *B) {
   return CBVH_OK;
 }
 
-void fill_params(Params &p, const cbvh_bvh *A, const cbvh_bvh *B) {
+void fill_params(Params &p, const cbvh_bvh *A, const cbvh_bvh *B, int mode) {
   std::memset(&p, 0, sizeof p);
   p.A = view(A);
   p.B = view(B);
-  p.L = make_layout(A, B);
+  p.L = make_layout(A, B, mode);
   p.wait_cap = g_wait_cap.load();
   for (int j = 0; j < kMaxK; ++j) {
     static const int n2[kMaxK] = {1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3};
@@ -1818,7 +1889,7 @@ extern "C" int cbvh_workspace_bytes(const cbvh_bvh *A, const cbvh_bvh *B, int64_
   if (!A || !B || !bytes || n < 0 || (mode != 0 && mode != 1)) return cbvh::fail(CBVH_ERR_ARG, "bad argument");
   int sms = 0;
   if (int rc = device_sms(&sms)) return rc;
-  *bytes = ws_plan(make_layout(A, B), n, mode, cap, sms).total;
+  *bytes = ws_plan(make_layout(A, B, mode), n, mode, cap, sms).total;
   return CBVH_OK;
 }
 
@@ -1837,7 +1908,7 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
   int sms = 0;
   if (int rc = device_sms(&sms)) return rc;
   Params p;
-  fill_params(p, A, B);
+  fill_params(p, A, B, 0);
   const WsPlan w = ws_plan(p.L, n, 0, want_pairs ? pair_capacity : 0, sms);
   if (!workspace || workspace_bytes < w.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
@@ -1909,7 +1980,7 @@ extern "C" int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *
   int sms = 0;
   if (int rc = device_sms(&sms)) return rc;
   Params p;
-  fill_params(p, A, B);
+  fill_params(p, A, B, 1);
   const WsPlan w = ws_plan(p.L, n, 1, 0, sms);
   if (!workspace || workspace_bytes < w.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return cbvh::fail(CBVH_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
@@ -2019,7 +2090,7 @@ extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const
   int sms = 0;
   if (int rc = device_sms(&sms)) return rc;
   Params p;
-  fill_params(p, A, B);
+  fill_params(p, A, B, 1);
   // carve the fixed array: counters, the chunk's flags, two task buffers, the ready flags,
   // then as many warp stacks as fit
   const int64_t o_flags = kWsHeader;
@@ -2129,6 +2200,8 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
       g.count = (int)idx.size();
       g.bases_at = (int64_t)b->bases.size();
       int tdA = 0, tdB = 0, sc = 1, mA = 2, mB = 2;
+      for (int64_t i : idx) mA = std::max(mA, q[i].A->m);
+      const int E = mode == 0 ? joint_pairs(mA) : 1;
       unsigned long long acc = 0;
       for (int64_t i : idx) {
         const cbvh_query_t &x = q[i];
@@ -2145,13 +2218,13 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
         acc += (unsigned long long)x.n;
         tdA = std::max(tdA, x.A->max_tdepth);
         tdB = std::max(tdB, x.B->max_tdepth);
-        sc = std::max(sc, stack_bound(x.A, x.B));
-        mA = std::max(mA, x.A->m);
+        sc = std::max(sc, stack_bound(x.A, x.B, E));
         mB = std::max(mB, x.B->m);
       }
       b->bases.push_back(acc);
       g.poses = (int64_t)acc;
-      g.L = warp_layout(K, tdA, tdB, sc, mA, mB);
+      g.L = warp_layout(K, tdA, tdB, sc, E * mA, mB);
+      g.L.E = E;
       g.A0 = view(q[idx[0]].A);
       g.B0 = view(q[idx[0]].B);
       g.pre_first = -1;
