@@ -57,9 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
     ap.add_argument("--arm-configs", type=int, default=200000)
-    ap.add_argument("--sections", default="batched,served,compression,refit,scale",
-                    help="comparisons run after the headline step: batched, served, compression, refit, "
-                         "scale (comma list)")
+    ap.add_argument("--sections", default="small,noalloc,batched,served,compression,refit,scale",
+                    help="comparisons run after the headline step: small, noalloc, batched, served, compression, "
+                         "refit, scale (comma list)")
     ap.add_argument("--scale-poses", type=int, default=1_000_000)
     ap.add_argument("--scale-pq-poses", type=int, default=20_000)
     ap.add_argument("--scale-pair-poses", type=int, default=100_000)
@@ -102,12 +102,20 @@ def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
 
 
 # ------------------------------------------------------------------ CPU (oracle) timing
-def oracle_rate(c, sample: int, target_s: float = 15.0):
+def oracle_rate(c, sample: int, target_s: float = 15.0, threads: int = 0):
     """Pose queries/s of the FP64 oracle (CD with pairs + PQ) on a bounded sample; the
-    sample grows until it takes about target_s seconds or reaches `sample` poses."""
+    sample grows until it takes about target_s seconds or reaches `sample` poses.
+    threads: OpenMP threads (0 = all the host's cores)."""
     import oracle
     A = oracle.BVH(*c["A"], K_DOP, BRANCH, BITS, TREELET)
     B = oracle.BVH(*c["B"], K_DOP, BRANCH, BITS, TREELET)
+    if threads:
+        all_threads = oracle.num_threads()
+        oracle.set_threads(threads)
+        try:
+            return oracle_rate(c, sample, target_s)
+        finally:
+            oracle.set_threads(all_threads)
     P = c["poses"]
     n, done, t_tot = 16, 0, 0.0
     while True:
@@ -580,6 +588,103 @@ def scale(cb, torch, dev, n_poses, pq_poses, pair_poses):
             "variants": out}
 
 
+def small_case(cb, torch, dev, launches=200):
+    """The small case exactly as configured: two displaced level-3 spheres (1,280 triangles
+    each), 18-DOP, branching 4, 16-bit deltas, 4 KB treelets; 256 poses, CD with sorted pair
+    lists, one query per launch.  Each launch is timed by CUDA events on its stream; the
+    inputs (a few hundred KB) stay in L2 from launch to launch, as they would in a loop of
+    such queries."""
+    import ctypes as C
+    L = cb.lib
+    c = synth.C1(256)
+    A = cb.BVH(*c["A"], 18, 4, 16, 4096, device=dev)
+    B = cb.BVH(*c["B"], 18, 4, 16, 4096, device=dev)
+    P = torch.as_tensor(c["poses"], device=dev)
+    n = len(c["poses"])
+    cap = int(cb.collide(A, B, P).pairs.shape[0] * 1.25) + 1024
+    hit = torch.empty(n, dtype=torch.uint8, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    prs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    need = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    wsb = cb.workspace_bytes(A, B, n, 0, cap)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    sp = cb._stream_ptr(None)
+    stream = torch.cuda.current_stream(dev)
+    ptr = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    args = (A.handle, B.handle, ptr(P), n, ptr(hit), ptr(off), ptr(prs), cap, ptr(need), cb.SORT_PAIRS, ptr(ws), wsb,
+            ptr(st), sp)
+    for _ in range(5):
+        L.cbvh_collide(*args)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(launches)]
+    n0 = cb.kernel_launches()
+    for a, b in ev:
+        a.record(stream)
+        rc = L.cbvh_collide(*args)
+        b.record(stream)
+        if rc:
+            raise cb.CbvhError(rc, L.cbvh_last_error().decode())
+    torch.cuda.synchronize()
+    kernels = (cb.kernel_launches() - n0) / launches
+    if int(st.item()):
+        raise cb.CbvhError(int(st.item()), "device status in the small case")
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    bv, leaf, _ = cb.query_stats(ws)
+    total = sum(ms)
+    return {"workload": "two displaced level-3 icospheres (1,280 tris each), 18-DOP, branching 4, 16-bit deltas, "
+                        "4 KB treelets; 256 poses, CD with sorted pair lists, one query per launch",
+            "launches": launches, "kernels_per_query": kernels, "pairs_per_query": int(need.item()),
+            "pose_queries_per_s": n * launches / (total / 1e3), "bv_pair_tests_per_s": bv * launches / (total / 1e3),
+            "latency_ms": {"p50": ms[len(ms) // 2], "p99": ms[min(len(ms) - 1, int(round(0.99 * (len(ms) - 1))))]}}
+
+
+def noalloc_compare(cb, torch, dev, A, B, poses, dist_out, ws_pq, flush, reps=3):
+    """The terrain step's proximity query through cbvh_distance_noalloc (fixed scratch inside
+    the library) beside cbvh_distance (caller's workspace); L2 flushed before each call,
+    CUDA events on the stream, the two results compared."""
+    import ctypes as C
+    L = cb.lib
+    sp = cb._stream_ptr(None)
+    stream = torch.cuda.current_stream(dev)
+    n = int(poses.shape[0])
+    ptr = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    out2 = torch.empty_like(dist_out)
+    st = torch.zeros(2, dtype=torch.int32, device=dev)
+    st1 = C.c_void_p(st.data_ptr() + 4)
+    calls = {"distance": lambda: L.cbvh_distance(A.handle, B.handle, ptr(poses), n, ptr(dist_out), ptr(ws_pq),
+                                                 ws_pq.numel(), ptr(st), sp),
+             "distance_noalloc": lambda: L.cbvh_distance_noalloc(A.handle, B.handle, ptr(poses), n, ptr(out2), st1, sp)}
+    res = {}
+    for name, fn in calls.items():
+        fn()
+        times = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc = fn()
+            b.record(stream)
+            if rc:
+                raise cb.CbvhError(rc, L.cbvh_last_error().decode())
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        res[name] = {"ms": statistics.median(times), "pose_queries_per_s": n / (statistics.median(times) / 1e3)}
+    if int(st.abs().sum().item()):
+        raise RuntimeError("device status in the allocation-free comparison")
+    res["max_abs_diff"] = float((dist_out - out2).abs().max().item())
+    res["workload"] = "terrain step's proximity query (10,000 poses), both passes"
+    return res
+
+
+def l2_ceiling(cb, dev):
+    """Measured L2 read bandwidth (GB/s): the best of three sizes that stay in L2."""
+    best = 0.0
+    for mb in (16, 32, 64):
+        best = max(best, cb.probe_l2_read(mb << 20, 20, device=dev))
+    return best
+
+
 # ------------------------------------------------------------------ engine
 def main():
     args = parse()
@@ -714,23 +819,53 @@ def main():
     pq_bytes = bv_pq * BYTES_BV + leaf_pq * BYTES_LEAF + n * BYTES_POSE
     cd_avg = prof["collide"][0] / max(1, prof["collide"][1])
     pq_avg = prof["distance"][0] / max(1, prof["distance"][1] // 2)  # two passes per distance query
-    dom = ("traverse_kernel<CD>", cd_bytes, cd_avg) if cd_avg >= pq_avg else ("traverse_kernel<PQ>", pq_bytes, pq_avg)
+    dom = (("traverse_kernel<CD>", cd_bytes, cd_avg, exp_cd) if cd_avg >= pq_avg
+           else ("traverse_kernel<PQ>", pq_bytes, pq_avg, exp_pq))
     achieved = dom[1] / (dom[2] / 1e3) / 1e9
-    # DRAM bytes per launch group from the committed ncu capture, only while the kernels are
-    # the ones it measured
+    # ncu counters of the traversal kernels from the committed capture, only while the
+    # kernels are the ones it measured: DRAM bytes per query (cold cache, the full-size
+    # launch list), L2 bytes and warp instructions per node-pair expansion (a smaller case,
+    # scaled by this run's expansion count)
     traffic = None
-    tr_file = os.path.join(ROOT, "profiles", "traffic.json")
+    ctr = {}
+    tr_file = os.path.join(ROOT, "profiles", "counters.json")
     if os.path.exists(tr_file):
         try:
             import hashlib
             tr = json.load(open(tr_file))
             src = open(os.path.join(ROOT, "paper_2012_05348_gb300", "csrc", "kernels.cu"), "rb").read()
             if tr.get("kernels_cu_sha1") == hashlib.sha1(src).hexdigest():
-                traffic = tr.get(dom[0])
+                ctr = tr.get(dom[0], {})
+                traffic = ctr.get("dram_bytes_per_query")
         except (OSError, ValueError):
             traffic = None
+    clocks = clk.summary()
+    sm_mhz = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    l2_gbs = l2_ceiling(cb, dev)
+    n_sm = props.multi_processor_count
+    issue_peak = n_sm * 4 * sm_mhz * 1e6  # one warp instruction per scheduler and cycle
+    l2 = {"achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+          "peak_source": "measured: cbvh_probe_l2_read, L1-bypassing 16-byte loads over an L2-resident buffer "
+                         "(best of 16, 32, 64 MB), this run",
+          "lts_bytes_per_query": None, "lts_frac": None}
+    issue = {"achieved": None, "peak": issue_peak, "unit": "warp instructions/s", "frac": None,
+             "peak_source": f"{n_sm} SMs x 4 schedulers x 1 warp instruction per cycle x {sm_mhz:.0f} MHz "
+                            "(median SM clock sampled during the timed steps)", "inst_per_query": None}
+    if ctr.get("lts_bytes_per_expansion"):
+        lts = ctr["lts_bytes_per_expansion"] * dom[3]
+        l2["lts_bytes_per_query"] = lts
+        l2["lts_frac"] = lts / (dom[2] / 1e3) / 1e9 / l2_gbs
+    if ctr.get("inst_per_expansion"):
+        inst = ctr["inst_per_expansion"] * dom[3]
+        issue["inst_per_query"] = inst
+        issue["achieved"] = inst / (dom[2] / 1e3)
+        issue["frac"] = issue["achieved"] / issue_peak
     extra = {}
     sections = set() if args.no_extra else {x.strip() for x in args.sections.split(",") if x.strip()}
+    if "small" in sections:
+        extra["small"] = small_case(cb, torch, dev)
+    if "noalloc" in sections:
+        extra["noalloc"] = noalloc_compare(cb, torch, dev, A, B, poses, dist_out, ws_pq, flush)
     if "batched" in sections:
         extra["batched"] = arm_sweep(cb, torch, dev, args.arm_configs)
     if "served" in sections:
@@ -757,8 +892,11 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, done, secs, cores = oracle_rate(c, args.cpu_sample)
+        rate1, done1, secs1, _ = oracle_rate(c, args.cpu_sample, target_s=6.0, threads=1)
         cpu = {"value": rate, "unit": "pose queries/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {done} poses of the 10,000-pose set, CD with pairs + PQ, {secs:.1f} s"}
+               "sample": f"first {done} poses of the 10,000-pose set, CD with pairs + PQ, {secs:.1f} s",
+               "single_thread": {"value": rate1, "cores": 1,
+                                 "sample": f"first {done1} poses, CD with pairs + PQ, {secs1:.1f} s"}}
     sm = sorted(step_ms)
     out = {
         "metric": METRIC, "value": value, "unit": "pose queries/s", "n_gpus": world, "steps": K,
@@ -781,12 +919,15 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_source": f"{peak_src} HBM copy bandwidth",
-                     "bytes": "algorithmic: BV tests x 34 B + leaf tests x 72 B + poses x 61 B (+ 12 B per pair)"},
+                     "bytes": "algorithmic: BV tests x 34 B + leaf tests x 72 B + poses x 61 B (+ 12 B per pair)",
+                     "l2": l2, "issue": issue,
+                     "binding": "instruction issue: the hierarchies stay in L2, so neither HBM nor L2 bandwidth is "
+                                "the limit; the issue fraction is the one to raise"},
         "kernel_ms": {"traverse_cd": cd_avg, "traverse_pq": pq_avg,
                       "compaction": prof["compaction"][0] / max(1, prof["compaction"][1])},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "pose queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "gpu_launches": gpu_launches,
     }
     out.update(extra)
