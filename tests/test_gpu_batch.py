@@ -5,7 +5,8 @@
 - The batch launch can be captured in a CUDA graph; replays reproduce the direct results,
   with every scheduler (rounds of handed-on tasks, one launch over a work queue, or
   rounds ending in a work-queue round).
-- A reduced arm-against-clutter sweep agrees with the FP64 oracle on poses away from contact.
+- A reduced arm-against-clutter sweep, and 1,000 configurations against the full clutter,
+  agree with the FP64 oracle on poses away from contact.
 """
 import numpy as np
 import pytest
@@ -132,6 +133,50 @@ def test_arm_sweep_against_oracle(cb, scene):
         assert (outs[i][:60][ok] == hit[ok]).all()
         checked += int(ok.sum())
     assert checked > 200
+
+
+@pytest.mark.parametrize("m,tb", [(8, 16384), (16, 4096)])
+def test_arm_sweep_full_clutter_against_oracle(cb, m, tb):
+    """The sweep as the benchmark runs it: the full 1,026,400-triangle clutter, 1,000
+    configurations x 6 links in one batch with early-exit collision, at the default
+    hierarchy (branching 8, 16 KB treelets) and at the one the autotuner picks on the box
+    (branching 16, 4 KB).  Flags equal the oracle's on every link pose away from contact,
+    and so does each configuration's answer (any link in collision) where all six are."""
+    import torch
+    n = 1000
+    c3 = synth.C3(n)
+    va = c3["A"][0]
+    clutter = cb.BVH(*c3["A"], 24, m, 8, tb)
+    links = [cb.BVH(*l, 24, m, 8, tb) for l in c3["links"]]
+    LP = [torch.as_tensor(np.ascontiguousarray(c3["link_poses"][:, i]), device="cuda") for i in range(6)]
+    items = [dict(A=clutter, B=L, kind="collide", poses=P, early_exit=True) for L, P in zip(links, LP)]
+    outs = np.stack([o.cpu().numpy() for o in cb.Batch(items).run()])
+    A = oracle.BVH(*c3["A"], 24, 8, 8, 16384)
+    o_hit = np.zeros((6, n), np.uint8)
+    near = np.zeros((6, n), bool)
+    for i, (v, t) in enumerate(c3["links"]):
+        B = oracle.BVH(v, t, 24, 8, 8, 16384)
+        P = c3["link_poses"][:, i]
+        near[i], _ = oracle.near_contact(A, B, P, 1e-6 * synth.scene_diameter(va, v))
+        o_hit[i], *_ = oracle.collide(A, B, P)
+    ok = ~near
+    assert (outs[ok] == o_hit[ok]).all(), np.argwhere((outs != o_hit) & ok)[:10]
+    all_clear = ok.all(0)
+    assert (outs.any(0)[all_clear] == o_hit.any(0)[all_clear]).all()
+    assert ok.sum() >= 3000 and o_hit[ok].sum() >= 500 and (o_hit[ok] == 0).sum() >= 1000
+    # the links as one configuration set: each configuration stops at its first colliding
+    # link, and the set's flag is the configuration's answer
+    sets = [dict(it, set="arm") for it in items]
+    batch = cb.Batch(sets)
+    for _ in range(2):  # the launch clears the set's flags: a second launch answers the same
+        souts = np.stack([o.cpu().numpy() for o in batch.run()])
+        anyh = batch.any_hit["arm"].cpu().numpy()
+        certain = (o_hit.astype(bool) & ok).any(0)
+        assert anyh[certain].all()
+        assert (anyh[all_clear] == o_hit.any(0)[all_clear]).all()
+        assert ((souts == 1) & ok <= (o_hit == 1)).all()  # an item's 1 is a real intersection
+        assert ((souts.any(0) == anyh.astype(bool))).all()
+        assert souts.sum() < outs.sum()  # configurations stopped at their first colliding link
 
 
 def test_arm_self_collision_against_oracle(cb, scene):
