@@ -63,9 +63,15 @@ def parse():
     ap.add_argument("--scale-poses", type=int, default=1_000_000)
     ap.add_argument("--scale-pq-poses", type=int, default=20_000)
     ap.add_argument("--scale-pair-poses", type=int, default=100_000)
+    ap.add_argument("--scale-variants", default="8:16384,16:16384,1:16384,0:16384,8:131072",
+                    help="storage modes of the scale comparison, bits:treelet_bytes (comma list)")
     ap.add_argument("--scale-only", action="store_true",
                     help="run only the scale-and-compression comparison (a profiling entry point)")
     return ap.parse_args()
+
+
+def scale_variants(args):
+    return tuple(tuple(int(x) for x in v.split(":")) for v in args.scale_variants.split(",") if v.strip())
 
 
 def dist_env():
@@ -238,8 +244,10 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
     CD for every configuration.  The autotuner first picks branching, treelet size,
     quantisation bits and launch options (work mapping, budget) on the first `tune_configs`
     configurations.  Then the whole sweep runs batched (one set of persistent launches over
-    all links, replayed from a CUDA graph) against the plain traversal (one query per link
-    and launch, one warp per pose) on the same hierarchies."""
+    all links, replayed from a CUDA graph; the six links of a configuration form one set, so
+    a configuration stops at its first colliding link) against the plain traversal (one
+    query per link and launch, one warp per pose) on the same hierarchies; both give every
+    configuration's answer (some link collides)."""
     from paper_2012_05348_gb300.autotune import DEFAULT_LAUNCH, apply, autotune_batch
     c = synth.C3(n_configs)
     LP = [torch.as_tensor(np.ascontiguousarray(c["link_poses"][:, i]), device=dev) for i in range(6)]
@@ -255,7 +263,7 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
     try:
         A = cb.BVH(*c["A"], 24, m, bits, tb, device=dev)
         links = [cb.BVH(*l, 24, m, bits, tb, device=dev) for l in c["links"]]
-        items = [dict(A=A, B=L, kind="collide", poses=P, early_exit=True) for L, P in zip(links, LP)]
+        items = [dict(A=A, B=L, kind="collide", poses=P, early_exit=True, set="arm") for L, P in zip(links, LP)]
         batch = cb.Batch(items, device=dev)
         outs = batch.run()
         g = torch.cuda.CUDAGraph()
@@ -268,7 +276,7 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
         with torch.cuda.graph(g):
             batch.launch()
         ms_batched = _events_ms(g.replay, torch)
-        collide_cfg = np.stack([o.cpu().numpy() for o in outs]).any(0)
+        collide_cfg = batch.any_hit["arm"].cpu().numpy().astype(bool)
         # self-collision: every non-adjacent link pair, link j posed in link i's frame
         sp = synth.self_pairs(6)
         rel = [torch.as_tensor(synth.relative_poses(c["link_poses"], i, j), device=dev) for i, j in sp]
@@ -279,11 +287,15 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
         ms_self = _events_ms(self_batch.run, torch)
         self_cfg = np.stack([o.cpu().numpy() for o in self_outs]).any(0)
 
+        plain_out = []
+
         def plain():
+            plain_out.clear()
             for L, P in zip(links, LP):
-                cb.collide(A, L, P, pairs=False, early_exit=True, check=False)
+                plain_out.append(cb.collide(A, L, P, pairs=False, early_exit=True, check=False).hit)
         cb.set_option(cb.OPT_SPLIT, cb.SPLIT_POSE)
         ms_plain = _events_ms(plain, torch, reps=2)
+        plain_cfg = torch.stack(plain_out).any(0).cpu().numpy()
     finally:
         apply({})
     q = 6 * n_configs
@@ -292,14 +304,18 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
             "autotuned": {"best": best, "sample_configurations": tune_configs, "candidates": len(trials),
                           "tuning_s": tune_s, "sample_ms_best": best_ms, "sample_ms_default": default_ms},
             "link_queries": q, "configs_in_collision": int(collide_cfg.sum()),
+            "answers_equal_plain": bool((plain_cfg == collide_cfg).all()),
             "self_collision": {"link_pairs": len(sp), "pair_queries": len(sp) * n_configs,
                                "configs_self_colliding": int(self_cfg.sum()), "ms": ms_self,
                                "pair_queries_per_s": len(sp) * n_configs / (ms_self / 1e3)},
             "configs_free": int((~collide_cfg & ~self_cfg).sum()),
             "batched_link_queries_per_s": q / (ms_batched / 1e3), "batched_ms": ms_batched,
             "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,
+            "batched_configurations_per_s": n_configs / (ms_batched / 1e3),
+            "plain_configurations_per_s": n_configs / (ms_plain / 1e3),
             "speedup_vs_plain": ms_plain / ms_batched,
-            "batched": "one graph-captured persistent launch set, autotuned hierarchy and launch options",
+            "batched": "one graph-captured persistent launch set, autotuned hierarchy and launch options, the six "
+                       "links of a configuration as one set (a configuration stops at its first colliding link)",
             "plain": "one cbvh_collide per link, one warp per pose, same hierarchies"}
 
 
@@ -495,7 +511,8 @@ def _bv_bytes(k: int, bits: int) -> int:
     return (k // 2) * 2 * w + 4 + 3 * 2 * w
 
 
-def scale(cb, torch, dev, n_poses, pq_poses, pair_poses):
+def scale(cb, torch, dev, n_poses, pq_poses, pair_poses,
+          variants=((8, 16384), (16, 16384), (1, 16384), (0, 16384), (8, 131072))):
     """Scale and compression: 32 fractal-displaced level-7 spheres (10,485,760 triangles) in a
     20 m cube, probed by a displaced level-6 sphere (81,920 triangles); 18-DOP, branching 4,
     bottom-up treelets.  For 8- and 16-bit deltas at 16 and 128 KB treelets and for FP32
@@ -558,7 +575,7 @@ def scale(cb, torch, dev, n_poses, pq_poses, pair_poses):
                 extra["hits"] = int(hit.sum().item())
             return ms, cb.query_stats(ws), extra
 
-        for bits, tb in [(8, 16384), (16, 16384), (1, 16384), (0, 16384), (8, 131072)]:
+        for bits, tb in variants:
             t0 = time.perf_counter()
             A = cb.BVH(*c["A"], 18, 4, bits, tb, device=dev)
             build_s = time.perf_counter() - t0
@@ -575,6 +592,11 @@ def scale(cb, torch, dev, n_poses, pq_poses, pair_poses):
                                  "pose_queries_per_s": pair_poses / (ms / 1e3), "pairs": ex["pairs"],
                                  "algorithmic_gbs": (bv * bvb + leaf * BYTES_LEAF + pair_poses * 57
                                                      + ex["pairs"] * 12) / (ms * 1e6)}
+            if not pq_poses:
+                out.append(r)
+                del A
+                torch.cuda.empty_cache()
+                continue
             ms, (bv, leaf, _), _ = run(A, pq_poses, "dist")
             r["pq"] = {"poses": pq_poses, "ms": ms, "pose_queries_per_s": pq_poses / (ms / 1e3), "bv_tests": bv,
                        "leaf_tests": leaf, "algorithmic_gbs": (bv * bvb + leaf * BYTES_LEAF + pq_poses * 52) / (ms * 1e6)}
@@ -699,7 +721,7 @@ def main():
     if args.scale_only:
         if rank == 0:
             print(json.dumps({"scale": scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses,
-                                             args.scale_pair_poses)}), flush=True)
+                                             args.scale_pair_poses, scale_variants(args))}), flush=True)
         return
     if world > 1:
         import torch.distributed as dist
@@ -888,7 +910,8 @@ def main():
         del c5
     if "scale" in sections:
         torch.cuda.empty_cache()
-        extra["scale"] = scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses, args.scale_pair_poses)
+        extra["scale"] = scale(cb, torch, dev, args.scale_poses, args.scale_pq_poses, args.scale_pair_poses,
+                               scale_variants(args))
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, done, secs, cores = oracle_rate(c, args.cpu_sample)

@@ -203,6 +203,14 @@ typedef struct {
   int64_t n;
   uint8_t *hit;       /* device, n bytes (mode 0) */
   float *dist;        /* device, n floats (mode 1) */
+  /* device, n bytes, or NULL (mode 0 only).  Items that pass the same array form one
+   * configuration set -- e.g. the links of a robot over one list of configurations, whose
+   * answer is "some link collides" -- and must have the same n.  The launch clears it;
+   * afterwards any_hit[i] = 1 iff pose i of some item of the set intersects.  Pose i of an
+   * item stops (or is never started) once another item of the set has set any_hit[i], so
+   * that item's own hit[i] is then 0: with a set, only any_hit and the items' 1s are
+   * exact. */
+  uint8_t *any_hit;
 } cbvh_query_t;
 
 typedef struct cbvh_batch cbvh_batch; /* opaque host-side plan of a batch */

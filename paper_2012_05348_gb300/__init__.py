@@ -309,20 +309,27 @@ def set_option(option: int, value: int) -> None:
 
 class _Query(C.Structure):
     _fields_ = [("A", C.c_void_p), ("B", C.c_void_p), ("mode", C.c_int32), ("flags", C.c_uint32),
-                ("poses", C.c_void_p), ("n", C.c_int64), ("hit", C.c_void_p), ("dist", C.c_void_p)]
+                ("poses", C.c_void_p), ("n", C.c_int64), ("hit", C.c_void_p), ("dist", C.c_void_p),
+                ("any_hit", C.c_void_p)]
 
 
 class Batch:
     """A batched query (cbvh_batch_*): many (A, B, kind, poses) work items run in one set of
     persistent launches.  Each item is a dict with keys A, B (BVH), kind ('collide' or
-    'distance'), poses (device float32 (n, 12)) and, for collisions, early_exit (bool).
-    Outputs are allocated here: ``outputs[i]`` is uint8 hit flags or float32 distances.
-    ``launch()`` only enqueues work on the stream, so it can be captured in a CUDA graph."""
+    'distance'), poses (device float32 (n, 12)) and, for collisions, early_exit (bool) and
+    set (any hashable): collision items with the same set share one per-pose flag,
+    ``any_hit[set]``, that is 1 iff some item of the set intersects at that pose, and each
+    pose stops as soon as one item of its set intersects (the links of one robot over one
+    list of configurations).  Outputs are allocated here: ``outputs[i]`` is uint8 hit flags
+    or float32 distances (with a set, an item's flag may be 0 where another item of the set
+    hit first).  ``launch()`` only enqueues work on the stream, so it can be captured in a
+    CUDA graph."""
 
     def __init__(self, items, device="cuda"):
         torch = _torch()
         self.items = items
         self.outputs = []
+        self.any_hit = {}
         arr = (_Query * max(1, len(items)))()
         for i, it in enumerate(items):
             poses = it["poses"]
@@ -330,11 +337,16 @@ class Batch:
             kind = 1 if it["kind"] == "distance" else 0
             if kind == 0:
                 out = torch.empty(n, dtype=torch.uint8, device=device)
+                anyp = None
+                if it.get("set") is not None:
+                    if it["set"] not in self.any_hit:
+                        self.any_hit[it["set"]] = torch.zeros(n, dtype=torch.uint8, device=device)
+                    anyp = self.any_hit[it["set"]].data_ptr()
                 arr[i] = _Query(it["A"].handle, it["B"].handle, 0, EARLY_EXIT if it.get("early_exit") else 0,
-                                poses.data_ptr(), n, out.data_ptr(), None)
+                                poses.data_ptr(), n, out.data_ptr(), None, anyp)
             else:
                 out = torch.empty(n, dtype=torch.float32, device=device)
-                arr[i] = _Query(it["A"].handle, it["B"].handle, 1, 0, poses.data_ptr(), n, None, out.data_ptr())
+                arr[i] = _Query(it["A"].handle, it["B"].handle, 1, 0, poses.data_ptr(), n, None, out.data_ptr(), None)
             self.outputs.append(out)
         self._arr = arr
         h = C.c_void_p()

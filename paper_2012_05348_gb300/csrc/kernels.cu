@@ -93,6 +93,7 @@ struct BatchItem {
   const float *poses;
   uint8_t *hit;
   float *dist;
+  uint8_t *any_hit;  // collision: per-pose flag shared by the items of one configuration set, or null
   uint32_t flags, pad;
 };
 
@@ -883,6 +884,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
   const BVd &B = BATCH ? bv[1] : p.B;
   const float *poses = p.poses;
   uint8_t *hitp = p.hit;
+  uint8_t *anyp = nullptr;  // batch items of one configuration set: "some item of this pose intersects"
   float *distp = p.dist;
   bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
   int item = -1;
@@ -979,6 +981,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         }
         poses = it.poses;
         hitp = it.hit;
+        anyp = it.any_hit;
         distp = it.dist;
         early = (it.flags & CBVH_EARLY_EXIT) != 0;
         item_lo = p.item_base[lo];
@@ -1025,14 +1028,17 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         if (lane == 0) distp[pose] = 0.f;
         continue;
       }
+      int settled = 0;
       if (lane == 0) {
         if (MODE == MODE_CD) {
           hitp[pose] = 0;
           if (p.counts) p.counts[pose] = 0;
+          if (BATCH && anyp) settled = *reinterpret_cast<volatile uint8_t *>(&anyp[pose]);
         } else {
           distp[pose] = INFINITY;
         }
       }
+      if (BATCH && MODE == MODE_CD && __shfl_sync(kFull, settled, 0)) continue;  // the set's answer is known
     } else if (MODE == MODE_PQ) {
       float v = 0.f;
       if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
@@ -1040,7 +1046,10 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       if (task_lb >= best) continue;  // a closer pair was found after this one was handed on
     } else if (early) {
       int h = 0;
-      if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
+      if (lane == 0) {
+        h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
+        if (BATCH && anyp) h |= *reinterpret_cast<volatile uint8_t *>(&anyp[pose]);
+      }
       if (__shfl_sync(kFull, h, 0)) continue;
     }
     float published = best;
@@ -1303,8 +1312,11 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
             best = fminf(best, __shfl_sync(kFull, v, 0));
           } else if (early) {
             int h = 0;
-            if (lane == 0) h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
-            if (__shfl_sync(kFull, h, 0)) done = true;  // another task of the pose found a pair
+            if (lane == 0) {
+              h = *reinterpret_cast<volatile uint8_t *>(&hitp[pose]);
+              if (BATCH && anyp) h |= *reinterpret_cast<volatile uint8_t *>(&anyp[pose]);
+            }
+            if (__shfl_sync(kFull, h, 0)) done = true;  // another task of the pose (or of its set) found a pair
           }
         }
         // PQ: entries whose lower bound reached the best distance found since they were
@@ -1348,6 +1360,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       if (MODE == MODE_CD) {
         if (nhits) {
           hitp[pose] = 1;
+          if (BATCH && anyp) anyp[pose] = 1;
           if (p.counts) atomicAdd(&p.counts[pose], nhits);
         }
       } else if (best < published) {
@@ -2159,6 +2172,7 @@ struct cbvh_batch {
   };
   std::vector<BatchItem> items;
   std::vector<unsigned long long> bases;
+  std::vector<std::pair<uint8_t *, int64_t>> any_hit;  // distinct per-set flag arrays, cleared at launch
   std::vector<Group> groups;
   int64_t o_ctr = 0, o_items = 0, o_bases = 0, o_tasks0 = 0, o_tasks1 = 0, o_ready = 0, o_stacks = 0, total = 0;
   uint32_t task_cap = 0;
@@ -2180,6 +2194,12 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
       return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": missing output");
     if (x.mode == 1 && x.flags) return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": flags are for collision");
     if (x.flags & ~CBVH_EARLY_EXIT) return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": unknown flags");
+    if (x.any_hit && x.mode != 0)
+      return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": any_hit is for collision queries");
+    for (int64_t k = 0; k < i && x.any_hit; ++k)
+      if (q[k].any_hit == x.any_hit && q[k].n != x.n)
+        return cbvh::fail(CBVH_ERR_ARG, "queries " + std::to_string(k) + " and " + std::to_string(i) +
+                                            " share any_hit but differ in pose count");
   }
   auto b = new cbvh_batch();
   if (int rc = device_sms(&b->sms)) {
@@ -2213,6 +2233,7 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
         it.hit = x.hit;
         it.dist = x.dist;
         it.flags = x.mode == 0 ? (x.flags | CBVH_EARLY_EXIT) : 0;  // collision items return flags only
+        it.any_hit = x.mode == 0 ? x.any_hit : nullptr;
         b->items.push_back(it);
         b->bases.push_back(acc);
         acc += (unsigned long long)x.n;
@@ -2243,8 +2264,15 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
       it.dist = nullptr;
       it.hit = nullptr;  // set at upload: the group's intersection flags + item base
       it.flags = CBVH_EARLY_EXIT;
+      it.any_hit = nullptr;
       b->items.push_back(it);
     }
+  }
+  for (int64_t i = 0; i < nq; ++i) {
+    if (!q[i].any_hit || q[i].n == 0) continue;
+    bool seen = false;
+    for (const auto &a : b->any_hit) seen |= a.first == q[i].any_hit;
+    if (!seen) b->any_hit.emplace_back(q[i].any_hit, q[i].n);
   }
   // workspace plan
   int64_t o = kWsHeader;
@@ -2317,6 +2345,8 @@ extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t w
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(ws, 0, b->o_items, s);  // header and round counters
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  for (const auto &a : b->any_hit)
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.first, 0, (size_t)a.second, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   const BatchItem *dev_items = reinterpret_cast<const BatchItem *>(ws + b->o_items);
   const unsigned long long *dev_bases = reinterpret_cast<const unsigned long long *>(ws + b->o_bases);
