@@ -1445,8 +1445,9 @@ __global__ void scatter_kernel(const uint32_t *triples, const unsigned long long
   }
 }
 
-// Sort each pose's pairs by (i, j): bitonic network whose first stage of every merge
-// compares mirrored elements, so that padding beyond the segment acts as +infinity.
+// Sort each pose's pairs by (i, j).  In shared memory: a bitonic network whose first stage of
+// every merge compares mirrored elements, so that padding beyond the segment acts as
+// +infinity.
 constexpr int kSortSmem = 4096;
 __device__ __forceinline__ void cmp_swap(unsigned long long *k, int i, int j) {
   unsigned long long a = k[i], b = k[j];
@@ -1473,8 +1474,36 @@ __device__ void bitonic(unsigned long long *k, int n) {
     }
   }
 }
+// Pairs of a segment as sort keys (i << 32 | j).
+__device__ __forceinline__ unsigned long long pair_key(const int32_t *pairs, int64_t q) {
+  return ((unsigned long long)(uint32_t)pairs[2 * q] << 32) | (uint32_t)pairs[2 * q + 1];
+}
+// Merge of the sorted runs L[0, m) and R[0, r) into out[0, m + r) by the block: each thread
+// finds where its share of the output starts on the merge path (binary search for the
+// number of its first outputs taken from L), then merges that share sequentially.
+__device__ void merge_runs(const unsigned long long *L, int m, const unsigned long long *R, int r,
+                           unsigned long long *out) {
+  const int total = m + r;
+  const int per = (total + blockDim.x - 1) / blockDim.x;
+  const int k0 = min(total, (int)threadIdx.x * per), k1 = min(total, k0 + per);
+  if (k0 >= k1) return;
+  int lo = max(0, k0 - r), hi = min(k0, m);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (L[mid] <= R[k0 - mid - 1])
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  int i = lo, j = k0 - lo;
+  for (int k = k0; k < k1; ++k) out[k] = (j >= r || (i < m && L[i] <= R[j])) ? L[i++] : R[j++];
+}
+// One block per pose (grid-stride).  A segment of at most kSortSmem pairs is sorted in shared
+// memory.  A longer one is sorted in runs of kSortSmem in shared memory, written to tmp (the
+// triples scratch, free once the scatter has run), then merged pairwise, alternating between
+// tmp and the segment itself, so that each pass reads and writes the segment once.
 __global__ void __launch_bounds__(256) sort_kernel(const int64_t *offsets, int64_t n, const unsigned long long *count,
-                                                   unsigned long long cap, int32_t *pairs) {
+                                                   unsigned long long cap, int32_t *pairs, unsigned long long *tmp) {
   __shared__ unsigned long long keys[kSortSmem];
   if (*count > cap) return;
   for (int64_t pose = blockIdx.x; pose < n; pose += gridDim.x) {
@@ -1482,15 +1511,38 @@ __global__ void __launch_bounds__(256) sort_kernel(const int64_t *offsets, int64
     const int cnt = (int)(offsets[pose + 1] - o);
     if (cnt < 2) continue;
     unsigned long long *seg = reinterpret_cast<unsigned long long *>(pairs + 2 * o);
-    unsigned long long *k = cnt <= kSortSmem ? keys : seg;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const uint32_t ai = (uint32_t)pairs[2 * (o + i)], bi = (uint32_t)pairs[2 * (o + i) + 1];
-      k[i] = ((unsigned long long)ai << 32) | bi;
+    unsigned long long *src = tmp + o, *dst = seg;
+    for (int c0 = 0; c0 < cnt; c0 += kSortSmem) {
+      const int len = min(kSortSmem, cnt - c0);
+      for (int i = threadIdx.x; i < len; i += blockDim.x) keys[i] = pair_key(pairs, o + c0 + i);
+      __syncthreads();
+      bitonic(keys, len);
+      if (cnt <= kSortSmem) {
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+          const unsigned long long v = keys[i];
+          pairs[2 * (o + i)] = (int32_t)(v >> 32);
+          pairs[2 * (o + i) + 1] = (int32_t)(v & 0xffffffffu);
+        }
+      } else {
+        for (int i = threadIdx.x; i < len; i += blockDim.x) src[c0 + i] = keys[i];
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    bitonic(k, cnt);
+    if (cnt <= kSortSmem) continue;
+    for (int w = kSortSmem; w < cnt; w *= 2) {
+      for (int r0 = 0; r0 < cnt; r0 += 2 * w) {
+        const int m = min(w, cnt - r0), r = max(0, min(w, cnt - r0 - w));
+        merge_runs(src + r0, m, src + r0 + m, r, dst + r0);
+      }
+      __syncthreads();
+      unsigned long long *t = src;
+      src = dst;
+      dst = t;
+    }
+    // keys back to (i, j) pairs; when they already sit in the segment, each thread rewrites
+    // the 8 bytes it read
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const unsigned long long v = k[i];
+      const unsigned long long v = src[i];
       pairs[2 * (o + i)] = (int32_t)(v >> 32);
       pairs[2 * (o + i) + 1] = (int32_t)(v & 0xffffffffu);
     }
@@ -1869,6 +1921,7 @@ void fill_params(Params &p, const cbvh_bvh *A, const cbvh_bvh *B, int mode) {
 }  // namespace
 
 extern "C" int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *stream) {
+  CBVH_RANGE("cbvh_attach");
   cbvh::clear_error();
   if (!h || !dev_blob) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   if (bytes < (int64_t)h->blob.size()) return cbvh::fail(CBVH_ERR_ARG, "device buffer smaller than the blob");
@@ -1886,6 +1939,7 @@ extern "C" int cbvh_attach(cbvh_bvh *h, void *dev_blob, int64_t bytes, void *str
 }
 
 extern "C" int cbvh_decode_all(const cbvh_bvh *h, int32_t *lattice_out, float *bounds_out, void *stream) {
+  CBVH_RANGE("cbvh_decode_all");
   cbvh::clear_error();
   if (!h) return cbvh::fail(CBVH_ERR_ARG, "NULL handle");
   if (!h->dev_blob) return cbvh::fail(CBVH_ERR_STATE, "handle has no device blob; call cbvh_attach");
@@ -1910,6 +1964,7 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
                             int64_t *pair_offsets, int32_t *pairs, int64_t pair_capacity, int64_t *pairs_needed,
                             uint32_t flags, void *workspace, int64_t workspace_bytes, int32_t *status,
                             void *stream) {
+  CBVH_RANGE("cbvh_collide");
   cbvh::clear_error();
   if (int rc = check_pair(A, B)) return rc;
   if (n < 0 || (n > 0 && (!poses || !hit)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
@@ -1971,7 +2026,8 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
     scatter_kernel<<<1024, 256, 0, s>>>(triples, p.pair_count, p.cap, pair_offsets, counts, pairs);
     g_launches.fetch_add(2);
     if (flags & CBVH_SORT_PAIRS) {
-      sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(pair_offsets, n, p.pair_count, p.cap, pairs);
+      sort_kernel<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, s>>>(
+          pair_offsets, n, p.pair_count, p.cap, pairs, reinterpret_cast<unsigned long long *>(triples));
       g_launches.fetch_add(1);
     }
     e = cudaGetLastError();
@@ -1986,6 +2042,7 @@ extern "C" int cbvh_collide(const cbvh_bvh *A, const cbvh_bvh *B, const float *p
 
 extern "C" int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist,
                              void *workspace, int64_t workspace_bytes, int32_t *status, void *stream) {
+  CBVH_RANGE("cbvh_distance");
   cbvh::clear_error();
   if (int rc = check_pair(A, B)) return rc;
   if (n < 0 || (n > 0 && (!poses || !dist)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
@@ -2065,9 +2122,9 @@ extern "C" int cbvh_profile_collect(double *ms_host, int64_t *launches_host) {
 // holds until the process exits: the counters of both passes, the intersection flags of one
 // chunk of poses, the two task buffers with the ready flags of a work-queue round, and the
 // per-warp stacks.  Calls share it, so calls that overlap on the GPU race.
-constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
-constexpr uint32_t kNoAllocTasks = 1u << 17;               // entries per task buffer
-constexpr int64_t kNoAllocChunk = int64_t(1) << 20;        // poses per chunk (one flag byte each)
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
+constexpr uint32_t kNoAllocTasks = 1u << 20;               // entries per task buffer
+constexpr int64_t kNoAllocChunk = int64_t(1) << 14;        // poses per chunk (one flag byte each)
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
@@ -2094,6 +2151,7 @@ int noalloc_scratch(void **out) {
 
 extern "C" int cbvh_distance_noalloc(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int64_t n, float *dist,
                                      int32_t *status, void *stream) {
+  CBVH_RANGE("cbvh_distance_noalloc");
   cbvh::clear_error();
   if (int rc = check_pair(A, B)) return rc;
   if (n < 0 || (n > 0 && (!poses || !dist)) || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL or negative argument");
@@ -2316,6 +2374,7 @@ extern "C" int cbvh_batch_workspace_bytes(const cbvh_batch *b, int64_t *bytes) {
 }
 
 extern "C" int cbvh_batch_upload(const cbvh_batch *b, void *workspace, int64_t workspace_bytes, void *stream) {
+  CBVH_RANGE("cbvh_batch_upload");
   cbvh::clear_error();
   if (!b) return cbvh::fail(CBVH_ERR_ARG, "NULL batch");
   if (!workspace || workspace_bytes < b->total || (reinterpret_cast<uintptr_t>(workspace) & 255))
@@ -2337,6 +2396,7 @@ extern "C" int cbvh_batch_upload(const cbvh_batch *b, void *workspace, int64_t w
 
 extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t workspace_bytes, int32_t *status,
                                  void *stream) {
+  CBVH_RANGE("cbvh_batch_launch");
   cbvh::clear_error();
   if (!b || !status) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   if (!workspace || workspace_bytes < b->total || (reinterpret_cast<uintptr_t>(workspace) & 255))

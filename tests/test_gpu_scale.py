@@ -88,6 +88,15 @@ def test_full_field_sampled_against_oracle(cb):
     pairs = _pairs_by_pose(res.offsets.cpu().numpy(), res.pairs.cpu().numpy())
     dist = cb.distance(A, B, Pd[:20_000]).cpu().numpy()
     assert (flags[:100_000] == hit).all()
+    # every pose's list sorted by (i, j), strictly: long lists (thousands of pairs) take the
+    # sort's merge passes
+    off = res.offsets.cpu().numpy()
+    ij = res.pairs.cpu().numpy().astype(np.int64)
+    keys = (ij[:, 0] << 32) | ij[:, 1]
+    inner = np.ones(len(keys) - 1, bool)
+    inner[off[1:-1][(off[1:-1] > 0) & (off[1:-1] < len(keys))] - 1] = False
+    assert (np.diff(keys)[inner] > 0).all()
+    assert np.diff(off).max() > 4 * 4096
     del res
     Ao = oracle.BVH(va, ta, 18, 4, 8, 16384, packing=oracle.PACKING_BOTTOM_UP)
     Bo = oracle.BVH(vb, tb, 18, 4, 8, 16384, packing=oracle.PACKING_BOTTOM_UP)
