@@ -168,12 +168,12 @@ int cbvh_distance(const cbvh_bvh *A, const cbvh_bvh *B, const float *poses, int6
  * The paper has no counterpart; it is a packaging of the same query.
  *   Schedule: cbvh_distance's two passes (early-exit collision, then branch and bound) with
  *   its work mapping and budgets (CBVH_OPT_SPLIT, CBVH_OPT_BUDGET0), run over chunks of at
- *   most 2^20 poses.
- *   Scratch: a fixed 32 MiB array inside the library, reserved on every GPU that loads it
+ *   most 2^14 poses (enough to fill the GPU, few enough for the task buffers below).
+ *   Scratch: a fixed 64 MiB array inside the library, reserved on every GPU that loads it
  *   until the process exits.  It holds the query's counters, the intersection flags of one
- *   chunk, two task buffers of 2^17 entries (cbvh_distance's workspace holds at least 2^22;
- *   tasks that find the buffer full run on where they are, which is slower on heavy pose
- *   sets but gives the same results) and one node-pair stack per warp, as many as fit.  A
+ *   chunk, two task buffers of 2^20 entries (a chunk of the terrain workload hands on about
+ *   52 tasks per pose; tasks that find the buffer full run on where they are, which is
+ *   slower but gives the same results) and one node-pair stack per warp, as many as fit.  A
  *   pair of hierarchies whose stack bound leaves room for fewer than 4 warps would be
  *   rejected with CBVH_ERR_WORKSPACE and a message giving the bytes needed; no pair this
  *   library builds comes near that (the bound is at most 4,336 entries, 52 KB a warp).
