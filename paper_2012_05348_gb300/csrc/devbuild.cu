@@ -659,6 +659,7 @@ extern "C" int cbvh_build_device_workspace_bytes(const cbvh_bvh *h, int64_t *byt
 
 extern "C" int cbvh_build_device(cbvh_bvh *h, const float *verts_dev, const int32_t *tris_dev, void *workspace,
                                  int64_t workspace_bytes, uint32_t flags, void *stream) {
+  CBVH_RANGE("cbvh_build_device");
   cbvh::clear_error();
   if (!h || !verts_dev || !tris_dev || !workspace) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   if (h->leaf_pos.empty()) return cbvh::fail(CBVH_ERR_STATE, "not a plan; create the handle with cbvh_build_plan");

@@ -6,6 +6,23 @@
 
 #include "cbvh.h"
 
+#if defined(__CUDACC__) || defined(CBVH_WITH_NVTX)
+#include <nvtx3/nvToolsExt.h>
+namespace cbvh {
+// Named NVTX range around a host entry point, for timeline tools (Nsight Systems and the
+// like); without a tool attached a push or pop is one check of a function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace cbvh
+#define CBVH_RANGE(name) cbvh::NvtxRange cbvh_nvtx_range_(name)
+#else
+#define CBVH_RANGE(name) ((void)0)
+#endif
+
 struct cbvh_bvh {
   // parameters
   int k = 0, K = 0, m = 0, bits = 0, treelet_bytes = 0;

@@ -273,6 +273,7 @@ extern "C" int cbvh_refit_workspace_bytes(const cbvh_bvh *h, int64_t *bytes) {
 }
 
 extern "C" int cbvh_refit_prepare(cbvh_bvh *h, void *workspace, int64_t workspace_bytes, void *stream) {
+  CBVH_RANGE("cbvh_refit_prepare");
   cbvh::clear_error();
   if (!h || !workspace) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   if (h->bits == CBVH_QUANT_SVB)  // a record's size follows its deltas: no re-encoding in place
@@ -358,6 +359,7 @@ extern "C" int cbvh_refit_prepare(cbvh_bvh *h, void *workspace, int64_t workspac
 
 extern "C" int cbvh_refit(cbvh_bvh *h, const float *verts_dev, int64_t n_verts, const int32_t *tris_dev,
                           void *workspace, int64_t workspace_bytes, int32_t *status, void *stream) {
+  CBVH_RANGE("cbvh_refit");
   cbvh::clear_error();
   if (!h || !verts_dev || !tris_dev || !status || !workspace) return cbvh::fail(CBVH_ERR_ARG, "NULL argument");
   if (!h->dev_blob) return cbvh::fail(CBVH_ERR_STATE, "handle has no device blob; call cbvh_attach");
