@@ -11,7 +11,13 @@ latency (submit to result) is recorded for p50 / p99.
 
 A robot is either one hierarchy or a chain of links (``robots``: name -> link model names);
 a request for a chain carries one pose per link and configuration, runs as one batch item
-per link, and resolves to "any link collides" or "smallest distance over the links".
+per link, and resolves to "any link collides" or "smallest distance over the links".  The
+links of a collision request form one configuration set of the batch, so a configuration
+stops at its first colliding link.
+
+A batch whose device status reports an error (for example a node-pair stack or a wait that
+ran out) does not fail its requests at once: each is retried once on the plain path, one
+query per model pair on the serving thread, and fails only if that fails too.
 """
 from __future__ import annotations
 
@@ -22,7 +28,7 @@ from concurrent.futures import Future
 
 import numpy as np
 
-from . import Batch, CbvhError, _torch
+from . import Batch, _torch, collide, distance
 
 
 def combine(kind: str, parts: list) -> np.ndarray:
@@ -64,6 +70,7 @@ class Server:
         self.cv = threading.Condition()
         self.latencies = []
         self.batches = 0
+        self.retries = 0
         self.running = True
         self.error = None
         self.thread = threading.Thread(target=self._loop, name="cbvh-serve", daemon=True)
@@ -104,8 +111,8 @@ class Server:
 
     def stats(self):
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
-        return dict(requests=len(self.latencies), batches=self.batches, p50_ms=float(np.percentile(lat, 50) * 1e3),
-                    p99_ms=float(np.percentile(lat, 99) * 1e3))
+        return dict(requests=len(self.latencies), batches=self.batches, retries=self.retries,
+                    p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3))
 
     # ---------------------------------------------------------------- serving thread
     @staticmethod
@@ -118,20 +125,42 @@ class Server:
     def _link_poses(r) -> int:
         return r.poses.shape[0] * (r.poses.shape[1] if r.poses.ndim == 3 else 1)
 
+    def _plain(self, r) -> np.ndarray:
+        """One request on the plain path: one query per model pair, synchronously."""
+        torch = _torch()
+        links = self.links(r.robot)
+        parts = []
+        for i, name in enumerate(links):
+            P = torch.as_tensor(np.ascontiguousarray(r.poses[:, i] if len(links) > 1 else r.poses),
+                                device=self.device)
+            if r.kind == "collide":
+                parts.append(collide(self.models[r.env], self.models[name], P, pairs=False,
+                                     early_exit=r.early_exit).hit.cpu().numpy())
+            else:
+                parts.append(distance(self.models[r.env], self.models[name], P).cpu().numpy())
+        return combine(r.kind, parts)
+
     def _complete(self, slot):
         ev, reqs, outs, nbytes, batch = self.busy[slot]
         ev.synchronize()
         code = int(batch.status.item())
-        now = time.perf_counter()
-        for r, parts in zip(reqs, outs):
-            r.t_done = now
-            self.latencies.append(now - r.t_submit)
-            if code != 0:
-                r.future.set_exception(CbvhError(code, "device status"))
-                continue
-            r.future.set_result(combine(r.kind, [o.numpy() for o in parts]))
         self.busy[slot] = None
         self.used -= nbytes
+        for r, parts in zip(reqs, outs):
+            if code != 0:  # retried once on the plain path
+                self.retries += 1
+                try:
+                    res = self._plain(r)
+                except Exception as e:  # noqa: BLE001 -- reported through the future
+                    res = e
+            else:
+                res = combine(r.kind, [o.numpy() for o in parts])
+            r.t_done = time.perf_counter()
+            self.latencies.append(r.t_done - r.t_submit)
+            if isinstance(res, Exception):
+                r.future.set_exception(res)
+            else:
+                r.future.set_result(res)
 
     def _admit(self):
         """Requests for the next batch: in arrival order, while memory and size allow."""
@@ -169,20 +198,25 @@ class Server:
             items, o = [], 0
             for r, name, P in parts:
                 n = len(P)
+                chain_cd = r.kind == "collide" and len(self.links(r.robot)) > 1
                 items.append(dict(A=self.models[r.env], B=self.models[name], kind=r.kind,
-                                  poses=dev[o:o + n], early_exit=r.early_exit))
+                                  poses=dev[o:o + n], early_exit=r.early_exit, set=id(r) if chain_cd else None))
                 o += n
             batch = Batch(items, device=self.device)
             batch.launch(stream)
             outs, k = [], 0
             for r in reqs:
+                nl = len(self.links(r.robot))
+                if r.kind == "collide" and nl > 1:  # the configuration set's answer
+                    srcs = [batch.any_hit[id(r)]]
+                else:
+                    srcs = batch.outputs[k:k + nl]
+                k += nl
                 mine = []
-                for _ in self.links(r.robot):
-                    out = batch.outputs[k]
+                for out in srcs:
                     h = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
                     h.copy_(out, non_blocking=True)
                     mine.append(h)
-                    k += 1
                 outs.append(mine)
             ev = torch.cuda.Event()
             ev.record(stream)

@@ -94,3 +94,36 @@ def test_served_results_equal_alone(cb, models, budget):
             assert (g == ref).all()
         else:
             assert np.allclose(g, ref, rtol=0, atol=1e-5 * 10.0)
+
+
+def test_failed_batch_retried_on_the_plain_path(cb, models):
+    """A batch whose device status reports an error is not lost: each of its requests is
+    retried once on the plain path and resolves to the result it has alone.  The error is
+    made on the host (the batch's status word is overwritten after its launch with the code
+    of an expired device wait); no kernel is made to fail."""
+    from paper_2012_05348_gb300.serve import Server
+
+    class Failing(Server):
+        def _launch(self, slot, reqs, nbytes):
+            super()._launch(slot, reqs, nbytes)
+            batch = self.busy[slot][4]
+            with _torch_stream(self.streams[slot]):
+                batch.status.fill_(-6)
+
+    reqs = _requests(23, 10)
+    srv = Failing(models, robots=ROBOTS)
+    futures = [srv.submit(env, robot, kind, P, early_exit=early) for env, robot, kind, P, early in reqs]
+    got = [f.result(timeout=120) for f in futures]
+    srv.close()
+    assert srv.stats()["retries"] == len(reqs)
+    for (env, robot, kind, P, early), g in zip(reqs, got):
+        ref = _alone(cb, models, env, robot, kind, P, early)
+        if kind == "collide":
+            assert (g == ref).all()
+        else:
+            assert np.allclose(g, ref, rtol=0, atol=1e-5 * 10.0)
+
+
+def _torch_stream(stream):
+    import torch
+    return torch.cuda.stream(stream)
