@@ -138,6 +138,25 @@ def test_brute_force_agrees_on_a_c1_subset(cb, c1):
     assert np.abs(d - b_d).max() <= TOL_PQ * c1["D"]
 
 
+@pytest.mark.parametrize("stage", [4096, 16384, 32768])
+def test_staged_treelets_against_oracle(cb, c1, stage):
+    """Treelet staging (Sec. III-B: treelets sized to a cache, here shared memory filled by
+    TMA bulk copies): with the leading treelets of both hierarchies read from shared memory
+    (one to eight of the small case's 4 KB treelets), collision is bit-exact and distances
+    within 1e-5 D against the oracle."""
+    o_hit, o_off, o_ij, _ = oracle.collide(c1["Ao"], c1["Bo"], c1["P"])
+    o_d, _ = oracle.distance(c1["Ao"], c1["Bo"], c1["P"])
+    cb.set_option(cb.OPT_STAGE_BYTES, stage)
+    try:
+        res = cb.collide(c1["A"], c1["B"], _gpu(c1["P"]))
+        d = cb.distance(c1["A"], c1["B"], _gpu(c1["P"])).cpu().numpy().astype(np.float64)
+    finally:
+        cb.set_option(cb.OPT_STAGE_BYTES, 0)
+    _check_cd(res, o_hit, o_off, o_ij)
+    assert np.abs(d - o_d).max() <= TOL_PQ * c1["D"]
+    assert ((d == 0) == (o_d == 0)).all()
+
+
 @pytest.mark.parametrize("k,m,bits,tb", [(6, 2, 8, 4096), (18, 4, 0, 4096), (18, 4, 8, 4096), (24, 8, 16, 16384),
                                          (26, 16, 16, 8192), (24, 16, 8, 131072), (18, 2, 16, 65536),
                                          (18, 4, 1, 4096), (24, 8, 1, 16384), (18, 4, 2, 4096), (24, 8, 2, 16384),
