@@ -39,6 +39,9 @@ extern "C" {
 #define CBVH_ERR_STACK (-5)     /* device: traversal stack bound exceeded (never by construction) */
 #define CBVH_ERR_TIMEOUT (-6)   /* device: a bounded wait ran out (CBVH_OPT_WAIT_CAP); results are incomplete */
 #define CBVH_ERR_WORKSPACE (-7) /* workspace smaller than cbvh_workspace_bytes() */
+#define CBVH_ERR_CHECK (-8)     /* device, checked build (libcbvh_checked.so) only: an index read from a blob or
+                                   computed by the traversal failed its bounds check; the access was skipped and
+                                   the results are not valid */
 #define CBVH_ERR_STATE (-9)     /* handle has no device blob attached */
 #define CBVH_ERR_IO (-10)       /* a file could not be read or written, or is not a valid hierarchy */
 

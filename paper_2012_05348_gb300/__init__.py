@@ -23,11 +23,13 @@ __all__ = ["BVH", "Batch", "collide", "distance", "probe_l2_read", "workspace_by
            "PACK_TOP_DOWN", "PACK_BOTTOM_UP", "SPLIT_POSE", "SPLIT_ROUNDS", "SPLIT_QUEUE", "SPLIT_ROUNDS_QUEUE", "SPLIT_AUTO",
            "SPLIT_DEFAULT", "BUDGET0_DEFAULT", "CbvhError", "lib", "LIB_PATH", "EARLY_EXIT", "SORT_PAIRS", "ERR"]
 
-LIB_PATH = _build.LIB
+# CBVH_CHECKED=1 in the environment loads the checked build (every index the traversal reads
+# from a blob or computes is bounds-checked into the status word, CBVH_ERR_CHECK)
+LIB_PATH = _build.LIB_CHECKED if os.environ.get("CBVH_CHECKED", "0") not in ("", "0") else _build.LIB
 EARLY_EXIT = 1
 SORT_PAIRS = 2
 ERR = {0: "OK", -1: "ARG", -2: "MESH", -3: "CUDA", -4: "CAPACITY", -5: "STACK", -6: "TIMEOUT", -7: "WORKSPACE",
-       -9: "STATE", -10: "IO"}
+       -8: "CHECK", -9: "STATE", -10: "IO"}
 
 
 

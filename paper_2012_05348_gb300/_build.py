@@ -1,5 +1,8 @@
 """Builds libcbvh.so in-tree: host builder (g++) and sm_103a kernels (nvcc), compiled in
-parallel and linked into one shared library with a static CUDA runtime."""
+parallel and linked into one shared library with a static CUDA runtime.  Beside it,
+libcbvh_checked.so: the same library with the traversal compiled with CBVH_CHECKED (every
+index read from a blob or computed by the traversal bounds-checked into the status word),
+loaded instead when the environment sets CBVH_CHECKED=1."""
 from __future__ import annotations
 
 import os
@@ -11,6 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcbvh.so")
+LIB_CHECKED = os.path.join(HERE, "libcbvh_checked.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -30,9 +34,9 @@ def sources():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB_CHECKED):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_CHECKED))
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
@@ -54,7 +58,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     refit_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "refit.cu"), "-o", obj_refit]
     devbuild_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "devbuild.cu"), "-o", obj_devbuild]
     probe_cmd = dev_cmd[:-4] + ["-c", os.path.join(CSRC, "probe.cu"), "-o", obj_probe]
-    cmds = (host_cmd, dev_cmd, refit_cmd, devbuild_cmd, probe_cmd)
+    obj_checked = os.path.join(BUILD_DIR, "kernels_checked.o")
+    checked_cmd = dev_cmd[:-4] + ["-DCBVH_CHECKED", "-c", os.path.join(CSRC, "kernels.cu"), "-o", obj_checked]
+    cmds = (host_cmd, dev_cmd, refit_cmd, devbuild_cmd, probe_cmd, checked_cmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
     for p, c, o in zip(procs, cmds, outs):
@@ -62,13 +68,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"build failed: {' '.join(c)}\n{o}")
         if verbose and o:
             print(o)
-    tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, obj_host, obj_dev, obj_refit, obj_devbuild,
-            obj_probe]
-    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")
-    os.replace(tmp, LIB)
+    for lib, kobj in ((LIB_CHECKED, obj_checked), (LIB, obj_dev)):
+        tmp = lib + f".tmp{os.getpid()}"
+        link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, obj_host, kobj, obj_refit, obj_devbuild,
+                obj_probe]
+        r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -66,6 +66,7 @@ struct BVd {
   float scale;                     // 2^e
   int K, bits, lbits, rec, root, tdepth;
   uint32_t lmask;
+  uint32_t n_treelets, n_tris;  // bounds of node references and leaf slots (checked build)
 };
 
 // Per-warp shared-memory layout (byte offsets inside the warp's slice).
@@ -138,6 +139,22 @@ struct Params {
 };
 
 __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
+
+// Checked build (compiled with CBVH_CHECKED into libcbvh_checked.so): every node reference,
+// record index, cache depth, leaf slot and leaf-queue position read from a blob or computed
+// by the traversal is checked before it is used; a failed check records CBVH_ERR_CHECK in the
+// query's status word and the access is skipped (the set is treated as empty, the slot as
+// 0), so the query ends with wrong results and a status that says so, never with an access
+// outside the blob or the warp's shared memory.  The default build compiles the checks out.
+#ifdef CBVH_CHECKED
+__device__ __noinline__ bool check_failed(int32_t *st) {
+  set_status(st, CBVH_ERR_CHECK);
+  return true;
+}
+#define CBVH_BAD(cond, st) ((cond) && check_failed(st))
+#else
+#define CBVH_BAD(cond, st) false
+#endif
 
 __device__ __forceinline__ const uint8_t *treelet_base(const BVd &X, uint32_t t) { return X.blob + X.toff[t]; }
 // Record of local node l in the treelet at tb: fixed-size records follow the root, Stream
@@ -237,6 +254,7 @@ struct Side {
   // locate the copy and its offset prefix in the dynamic shared memory
   uint32_t st_cnt;
   int st_off, st_toff;
+  int32_t *status;  // the query's status word (checked build)
 };
 
 extern __shared__ __align__(128) uint8_t g_dsmem[];
@@ -286,6 +304,7 @@ __device__ void chain_decode(const BVd &X, Side &S, uint32_t x, uint32_t w0, con
     if (lane == 0) S.path[dd] = (int)ll;
     if (dd == 0) break;
     ll = w & 0xffffu;  // the parent: in depth-first order usually cached, so look before loading
+    if (CBVH_BAD(ll >= ld32(S.cur_base), S.status)) ll = 0;
     --dd;
     if (S.tag[dd] == (tb | ll)) {
       start = dd;
@@ -324,14 +343,20 @@ template <int ND, bool VAR, bool LAT>
 __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, int lane, float2 *iv, int KS,
                           uint32_t *ref, uint32_t *leaf, int *shift, bool leaf_bounds = true) {
   const uint32_t t = x >> X.lbits;
+  if (CBVH_BAD(t >= X.n_treelets, S.status)) return 0;
   if (t != S.cur_t) {
     S.cur_t = t;
     S.cur_base = tbase(X, S, t);
   }
+  if (CBVH_BAD((x & X.lmask) >= ld32(S.cur_base), S.status)) return 0;
   const uint8_t *rx = rec_at<VAR>(X, S.cur_base, x & X.lmask);
   const uint32_t w0 = ld32(rx), w1 = ld32(rx + 4);
   const int nc = (int)((w0 >> 16) & 31u);
   const bool ext = (w0 >> 21) & 1u;
+  if (CBVH_BAD(nc > kMaxM || (int)(w0 >> 24) > X.tdepth ||
+                   (nc == 0 ? w1 >= X.n_tris : (ext ? w1 + nc > X.n_treelets : w1 + nc > ld32(S.cur_base))),
+               S.status))
+    return 0;
   const bool self = force_self || nc == 0;
   constexpr int nd = ND;
   if (self && nc == 0 && !leaf_bounds) {  // a leaf standing for itself, bounded by its triangle
@@ -364,8 +389,10 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
         iv[i * KS + j] = abs_bound(rc, j, X.bits);
         if (j == 0) {
           const uint32_t cw0 = ld32(rc);
+          uint32_t sl = ((cw0 >> 16) & 31u) == 0 ? ld32(rc + 4) : 0xffffffffu;
+          if (CBVH_BAD(sl != 0xffffffffu && sl >= X.n_tris, S.status)) sl = 0;
           ref[i] = cref;
-          leaf[i] = ((cw0 >> 16) & 31u) == 0 ? ld32(rc + 4) : 0xffffffffu;
+          leaf[i] = sl;
         }
       }
     }
@@ -405,8 +432,10 @@ __device__ int decode_set(const BVd &X, Side &S, uint32_t x, bool force_self, in
     iv[i * KS + j] = lat_to_f(L, X.scale);
     if (j == 0) {
       const uint32_t cw0 = ld32(rc);
+      uint32_t sl = ((cw0 >> 16) & 31u) == 0 ? ld32(rc + 4) : 0xffffffffu;
+      if (CBVH_BAD(sl != 0xffffffffu && sl >= X.n_tris, S.status)) sl = 0;
       ref[i] = cref;
-      leaf[i] = ((cw0 >> 16) & 31u) == 0 ? ld32(rc + 4) : 0xffffffffu;
+      leaf[i] = sl;
     }
   }
   __syncwarp();
@@ -851,7 +880,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
           nullptr,
           staged ? (uint32_t)p.L.st_cnt[0] : 0u,
           p.L.st_off[0],
-          p.L.st_toff[0]};
+          p.L.st_toff[0],
+          p.status};
   Side SB{reinterpret_cast<uint32_t *>(ws + p.L.o_tagB),
           reinterpret_cast<int2 *>(ws + p.L.o_latB),
           reinterpret_cast<int *>(ws + p.L.o_pathB),
@@ -860,7 +890,8 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
           nullptr,
           staged ? (uint32_t)p.L.st_cnt[1] : 0u,
           p.L.st_off[1],
-          p.L.st_toff[1]};
+          p.L.st_toff[1],
+          p.status};
   float2 *aiv = reinterpret_cast<float2 *>(ws + p.L.o_aset);  // A members' slabs (lo, hi) [i][KS]
   const int MA = p.L.MA, MB = p.L.MB;
   uint32_t *aref = reinterpret_cast<uint32_t *>(aiv + MA * KS);
@@ -1240,6 +1271,10 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         const bool isleaf = keep && aleaf[i] != 0xffffffffu && bleaf[j] != 0xffffffffu;
         const unsigned ml = __ballot_sync(kFull, isleaf);
         const unsigned mi = __ballot_sync(kFull, keep && !isleaf);
+        if (CBVH_BAD(nleaf + __popc(ml) > p.L.leafq_cap, p.status)) {
+          done = true;
+          break;
+        }
         if (sp + __popc(mi) > p.L.stack_cap) {
           if (lane == 0) set_status(p.status, CBVH_ERR_STACK);
           done = true;
@@ -1597,6 +1632,8 @@ BVd view(const cbvh_bvh *h) {
   v.root = h->root_bytes;
   v.tdepth = h->max_tdepth;
   v.lmask = (h->lbits >= 32) ? 0xffffffffu : ((1u << h->lbits) - 1u);
+  v.n_treelets = (uint32_t)h->n_treelets;
+  v.n_tris = (uint32_t)h->n_tris;
   return v;
 }
 

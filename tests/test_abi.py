@@ -29,11 +29,14 @@ def declared_symbols():
 
 
 def test_library_exports_every_declared_symbol(cb):
+    """Both builds: libcbvh.so and the bounds-checked libcbvh_checked.so."""
+    from paper_2012_05348_gb300 import _build
     syms = declared_symbols()
     assert len(syms) >= 10
-    lib = C.CDLL(cb.LIB_PATH)
-    for s in syms:
-        assert hasattr(lib, s), s
+    for path in (_build.LIB, _build.LIB_CHECKED):
+        lib = C.CDLL(path)
+        for s in syms:
+            assert hasattr(lib, s), (path, s)
 
 
 CONFIGS = [(18, 4, 16, 4096), (24, 8, 8, 16384), (6, 2, 8, 4096), (26, 16, 16, 8192), (18, 4, 0, 4096),
