@@ -324,19 +324,27 @@ def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 100
     """Request loop under open-loop Poisson arrivals (the serving workload: terrain and clutter
     environments; the 6-link arm and the level-5 and level-3 spheres as robots; collision and
     distance 1:1; log-uniform 1..4096 configurations per request).  Each offered rate runs
-    for min(2 s, max_requests / rate) of arrivals.  Reports p50/p99 latency and throughput;
+    for min(2 s, max_requests / rate) of arrivals; the last rate's mix is then replayed at
+    50 % and 80 % of its served rate.  Reports p50/p99 latency and throughput;
     the plain form serves the same requests one call per model pair (per link for the arm),
     in arrival order."""
     from paper_2012_05348_gb300.serve import Server
     import threading
     out = []
-    # the listed rates, then 50 % and 80 % of the saturation rate they measured (the largest
-    # served request rate), each with arrivals for up to 4 s
+    # the listed rates; then the last rate's request mix replayed at 50 % and 80 % of the
+    # request rate it was served at (its saturation rate: at that offered rate every request
+    # arrives while the server is busy), the Poisson gaps rescaled to the new rate
     todo = [(r, None) for r in rates]
+    last = None
     while todo:
         rate, frac = todo.pop(0)
-        secs = min(2.0 if frac is None else 4.0, max_requests / rate)
-        gaps, reqs = synth.C4(rate, secs, height_fn, seed=seed + int(rate) + (7 if frac else 0))
+        if frac is None:
+            secs = min(2.0, max_requests / rate)
+            gaps, reqs = synth.C4(rate, secs, height_fn, seed=seed + int(rate))
+        else:
+            gaps0, reqs, rate0 = last
+            gaps = [g * rate0 / rate for g in gaps0]
+            secs = float(sum(gaps))
         srv = Server(models, mem_budget=8 << 30, device=dev, robots=robots)
         futs = []
 
@@ -382,8 +390,10 @@ def serving(cb, torch, dev, models, robots, height_fn, rates=(20, 100, 2000, 100
                     "speedup_vs_plain": t_plain / (t_end - t_start)})
         if frac is not None:
             out[-1]["fraction_of_saturation"] = frac
-        if not todo and all(o.get("fraction_of_saturation") is None for o in out):
-            sat = max(o["served_req_per_s"] for o in out)
+            out[-1]["request_mix"] = f"that of {last[2]:g} req/s, gaps rescaled"
+        if not todo and frac is None:
+            last = (gaps, reqs, rate)
+            sat = out[-1]["served_req_per_s"]
             todo = [(0.5 * sat, 0.5), (0.8 * sat, 0.8)]
     return out
 

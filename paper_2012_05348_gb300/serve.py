@@ -54,7 +54,7 @@ class Server:
     an arm); a plain model name also serves as a robot.  mem_budget: device bytes that batches
     in flight may use.  max_poses: cap on the link poses of one batch."""
 
-    def __init__(self, models: dict, mem_budget: int = 1 << 30, slots: int = 2, max_poses: int = 1 << 16,
+    def __init__(self, models: dict, mem_budget: int = 1 << 30, slots: int = 4, max_poses: int = 1 << 16,
                  device="cuda", robots: dict | None = None):
         torch = _torch()
         self.models = models
