@@ -239,6 +239,22 @@ def _events_ms(fn, torch, reps=3):
     return e0.elapsed_time(e1) / reps
 
 
+def _launch_latencies(fn, torch, reps=7):
+    """p50 / p99 of single launches of fn, each timed by its own CUDA events after a warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return {"p50": ts[len(ts) // 2], "p99": ts[min(len(ts) - 1, int(round(0.99 * (len(ts) - 1))))], "launches": reps}
+
+
 def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
     """Motion-planning sweep: 6 arm links against a 1,026,400-triangle clutter scene, early-exit
     CD for every configuration.  The autotuner first picks branching, treelet size,
@@ -276,6 +292,7 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
         with torch.cuda.graph(g):
             batch.launch()
         ms_batched = _events_ms(g.replay, torch)
+        lat_batched = _launch_latencies(g.replay, torch)
         collide_cfg = batch.any_hit["arm"].cpu().numpy().astype(bool)
         # self-collision: every non-adjacent link pair, link j posed in link i's frame
         sp = synth.self_pairs(6)
@@ -310,6 +327,7 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
                                "pair_queries_per_s": len(sp) * n_configs / (ms_self / 1e3)},
             "configs_free": int((~collide_cfg & ~self_cfg).sum()),
             "batched_link_queries_per_s": q / (ms_batched / 1e3), "batched_ms": ms_batched,
+            "batched_latency_ms": dict(lat_batched, per="graph replay of the whole sweep"),
             "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,
             "batched_configurations_per_s": n_configs / (ms_batched / 1e3),
             "plain_configurations_per_s": n_configs / (ms_plain / 1e3),

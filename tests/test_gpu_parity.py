@@ -157,6 +157,29 @@ def test_staged_treelets_against_oracle(cb, c1, stage):
     assert ((d == 0) == (o_d == 0)).all()
 
 
+@pytest.mark.parametrize("split,budget0", [(0, 256), (1, 16), (2, 16), (3, 16), (4, 1)])
+def test_work_mappings_against_oracle(cb, c1, split, budget0):
+    """Every work mapping -- one warp per pose to the end, rounds of handed-on tasks, one
+    launch over a work queue with donation, rounds ending in a queue round -- with small
+    budgets so that tasks are handed on and donated often: collision bit-exact and
+    distances within 1e-5 D against the oracle."""
+    o_hit, o_off, o_ij, _ = oracle.collide(c1["Ao"], c1["Bo"], c1["P"])
+    o_d, _ = oracle.distance(c1["Ao"], c1["Bo"], c1["P"])
+    cb.set_option(cb.OPT_SPLIT, split)
+    cb.set_option(cb.OPT_BUDGET0, budget0)
+    try:
+        res = cb.collide(c1["A"], c1["B"], _gpu(c1["P"]))
+        flags = cb.collide(c1["A"], c1["B"], _gpu(c1["P"]), pairs=False).hit.cpu().numpy()
+        d = cb.distance(c1["A"], c1["B"], _gpu(c1["P"])).cpu().numpy().astype(np.float64)
+    finally:
+        cb.set_option(cb.OPT_SPLIT, cb.SPLIT_DEFAULT)
+        cb.set_option(cb.OPT_BUDGET0, cb.BUDGET0_DEFAULT)
+    _check_cd(res, o_hit, o_off, o_ij)
+    assert (flags == o_hit).all()
+    assert np.abs(d - o_d).max() <= TOL_PQ * c1["D"]
+    assert ((d == 0) == (o_d == 0)).all()
+
+
 @pytest.mark.parametrize("k,m,bits,tb", [(6, 2, 8, 4096), (18, 4, 0, 4096), (18, 4, 8, 4096), (24, 8, 16, 16384),
                                          (26, 16, 16, 8192), (24, 16, 8, 131072), (18, 2, 16, 65536),
                                          (18, 4, 1, 4096), (24, 8, 1, 16384), (18, 4, 2, 4096), (24, 8, 2, 16384),
