@@ -66,9 +66,9 @@ def test_distance_noalloc_matches_the_oracle_on_two_calls(cb):
 
 
 def test_distance_noalloc_sequence_of_different_pairs(cb):
-    """Spheres, then the terrain at the full 10,000 poses (enough handed-on work to fill the
-    fixed task buffers), then the spheres again: each call equals cbvh_distance, whatever
-    the previous call left in the shared array."""
+    """Spheres, then the terrain at the full 10,000 poses (about half a million tasks handed
+    on between rounds, half the fixed task buffers), then the spheres again: each call
+    equals cbvh_distance, whatever the previous call left in the shared array."""
     import torch
     s = synth.C1(300)
     t = synth.C2(10000)
