@@ -117,8 +117,9 @@ class Server:
     # ---------------------------------------------------------------- serving thread
     @staticmethod
     def _bytes(n_poses: int) -> int:
-        # poses + outputs + the batch workspace: two task buffers of 16-byte entries and their
-        # ready flags (at least 2^22 entries, else 512 per pose) + stacks and counters
+        # admission estimate of a batch: poses + outputs + the batch workspace: two task buffers
+        # of 16-byte entries and their ready flags (at least 2^22 entries, else 512 per pose) +
+        # stacks and counters (the launch then charges the plan's exact workspace)
         return n_poses * (48 + 4 + 1) + max(1 << 22, 512 * n_poses) * (2 * 16 + 4) + (96 << 20)
 
     @staticmethod
@@ -178,7 +179,9 @@ class Server:
             need = b
         return take, need
 
-    def _launch(self, slot, reqs, nbytes):
+    def _launch(self, slot, reqs, est_bytes):
+        """Launch one batch of the admitted requests on the slot's stream (est_bytes: the
+        admission estimate; the slot is charged the batch's exact bytes)."""
         torch = _torch()
         stream = self.streams[slot]
         with torch.cuda.stream(stream):
@@ -220,6 +223,11 @@ class Server:
                 outs.append(mine)
             ev = torch.cuda.Event()
             ev.record(stream)
+        # charge what the batch holds: its poses and outputs and the workspace its plan asked
+        # for (task buffers sized by its pose count, one node-pair stack per resident warp);
+        # admission used the estimate, which leaves out the stacks' dependence on the depths
+        nbytes = int(dev.numel()) * 4 + sum(int(o.numel()) * o.element_size() for o in batch.outputs) + \
+            int(batch.workspace.numel())
         self.busy[slot] = (ev, reqs, outs, nbytes, batch)
         self.used += nbytes
         self.batches += 1
