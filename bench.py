@@ -304,6 +304,29 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
         ms_self = _events_ms(self_batch.run, torch)
         self_cfg = np.stack([o.cpu().numpy() for o in self_outs]).any(0)
 
+        # clearance: the smallest distance over the six links of each configuration, as one
+        # distance set (each link prunes with the configuration's best so far), against the
+        # same items without the set and one cbvh_distance per link
+        n_cl = min(4096, n_configs)
+        LPc = [P[:n_cl] for P in LP]
+        cl_set = cb.Batch([dict(A=A, B=L, kind="distance", poses=P, set="arm") for L, P in zip(links, LPc)], device=dev)
+        cl_items = cb.Batch([dict(A=A, B=L, kind="distance", poses=P) for L, P in zip(links, LPc)], device=dev)
+        ms_cl_set = _events_ms(cl_set.run, torch, reps=2)
+        ms_cl_items = _events_ms(cl_items.run, torch, reps=2)
+        cl_plain = []
+
+        def cl_plain_fn():
+            cl_plain.clear()
+            for L, P in zip(links, LPc):
+                cl_plain.append(cb.distance(A, L, P, check=False))
+        ms_cl_plain = _events_ms(cl_plain_fn, torch, reps=1)
+        cl_ref = torch.stack(cl_plain).min(0).values
+        cl_diff = float((cl_set.min_dist["arm"] - cl_ref).abs().max().item())
+        clearance = {"configurations": n_cl, "set_ms": ms_cl_set, "items_ms": ms_cl_items, "plain_ms": ms_cl_plain,
+                     "set_configurations_per_s": n_cl / (ms_cl_set / 1e3),
+                     "speedup_set_vs_items": ms_cl_items / ms_cl_set, "speedup_set_vs_plain": ms_cl_plain / ms_cl_set,
+                     "max_abs_diff_vs_plain": cl_diff,
+                     "what": "smallest distance over the six links of each configuration"}
         plain_out = []
 
         def plain():
@@ -330,6 +353,7 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
             "batched_latency_ms": dict(lat_batched, per="graph replay of the whole sweep"),
             "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,
             "batched_configurations_per_s": n_configs / (ms_batched / 1e3),
+            "clearance": clearance,
             "plain_configurations_per_s": n_configs / (ms_plain / 1e3),
             "speedup_vs_plain": ms_plain / ms_batched,
             "batched": "one graph-captured persistent launch set, autotuned hierarchy and launch options, the six "

@@ -214,6 +214,14 @@ typedef struct {
    * that item's own hit[i] is then 0: with a set, only any_hit and the items' 1s are
    * exact. */
   uint8_t *any_hit;
+  /* device, n floats, or NULL (mode 1 only).  Distance items that pass the same array form
+   * a configuration set (e.g. the links of a robot, whose clearance is the smallest distance
+   * over its links) and must have the same n.  The launch resets it; afterwards
+   * min_dist[i] is the smallest distance over the set's items at pose i, within the
+   * distance tolerance of cbvh_distance.  Each item prunes with the set's best distance so
+   * far, so an item's own dist[i] is then only an upper bound of its distance (a distance
+   * of one of its own triangle pairs, or +inf), exact where it is the set's minimum. */
+  float *min_dist;
 } cbvh_query_t;
 
 typedef struct cbvh_batch cbvh_batch; /* opaque host-side plan of a batch */

@@ -312,7 +312,7 @@ def set_option(option: int, value: int) -> None:
 class _Query(C.Structure):
     _fields_ = [("A", C.c_void_p), ("B", C.c_void_p), ("mode", C.c_int32), ("flags", C.c_uint32),
                 ("poses", C.c_void_p), ("n", C.c_int64), ("hit", C.c_void_p), ("dist", C.c_void_p),
-                ("any_hit", C.c_void_p)]
+                ("any_hit", C.c_void_p), ("min_dist", C.c_void_p)]
 
 
 class Batch:
@@ -322,9 +322,12 @@ class Batch:
     set (any hashable): collision items with the same set share one per-pose flag,
     ``any_hit[set]``, that is 1 iff some item of the set intersects at that pose, and each
     pose stops as soon as one item of its set intersects (the links of one robot over one
-    list of configurations).  Outputs are allocated here: ``outputs[i]`` is uint8 hit flags
-    or float32 distances (with a set, an item's flag may be 0 where another item of the set
-    hit first).  ``launch()`` only enqueues work on the stream, so it can be captured in a
+    list of configurations); distance items with the same set share one per-pose minimum,
+    ``min_dist[set]``, the smallest distance over the set's items, and each item prunes
+    with the set's best distance so far.  Outputs are allocated here: ``outputs[i]`` is
+    uint8 hit flags or float32 distances (with a set, an item's flag may be 0 where another
+    item of the set hit first, and an item's distance is only exact where it is the set's
+    minimum).  ``launch()`` only enqueues work on the stream, so it can be captured in a
     CUDA graph."""
 
     def __init__(self, items, device="cuda"):
@@ -332,6 +335,7 @@ class Batch:
         self.items = items
         self.outputs = []
         self.any_hit = {}
+        self.min_dist = {}
         arr = (_Query * max(1, len(items)))()
         for i, it in enumerate(items):
             poses = it["poses"]
@@ -348,7 +352,13 @@ class Batch:
                                 poses.data_ptr(), n, out.data_ptr(), None, anyp)
             else:
                 out = torch.empty(n, dtype=torch.float32, device=device)
-                arr[i] = _Query(it["A"].handle, it["B"].handle, 1, 0, poses.data_ptr(), n, None, out.data_ptr(), None)
+                mind = None
+                if it.get("set") is not None:
+                    if it["set"] not in self.min_dist:
+                        self.min_dist[it["set"]] = torch.empty(n, dtype=torch.float32, device=device)
+                    mind = self.min_dist[it["set"]].data_ptr()
+                arr[i] = _Query(it["A"].handle, it["B"].handle, 1, 0, poses.data_ptr(), n, None, out.data_ptr(), None,
+                                mind)
             self.outputs.append(out)
         self._arr = arr
         h = C.c_void_p()

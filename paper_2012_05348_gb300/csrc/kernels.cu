@@ -95,6 +95,7 @@ struct BatchItem {
   uint8_t *hit;
   float *dist;
   uint8_t *any_hit;  // collision: per-pose flag shared by the items of one configuration set, or null
+  float *min_dist;   // distance: per-pose minimum shared by the items of one configuration set, or null
   uint32_t flags, pad;
 };
 
@@ -916,6 +917,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
   const float *poses = p.poses;
   uint8_t *hitp = p.hit;
   uint8_t *anyp = nullptr;  // batch items of one configuration set: "some item of this pose intersects"
+  float *mindp = nullptr;   // ... and "the smallest distance any item of this pose has found"
   float *distp = p.dist;
   bool early = (p.flags & CBVH_EARLY_EXIT) != 0;
   int item = -1;
@@ -1013,6 +1015,7 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         poses = it.poses;
         hitp = it.hit;
         anyp = it.any_hit;
+        mindp = it.min_dist;
         distp = it.dist;
         early = (it.flags & CBVH_EARLY_EXIT) != 0;
         item_lo = p.item_base[lo];
@@ -1056,10 +1059,14 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
     float best = INFINITY;
     if (root) {
       if (MODE == MODE_PQ && p.skip && p.skip[gid]) {  // intersecting: the distance is 0
-        if (lane == 0) distp[pose] = 0.f;
+        if (lane == 0) {
+          distp[pose] = 0.f;
+          if (BATCH && mindp) atomicMin(reinterpret_cast<unsigned int *>(&mindp[pose]), 0u);
+        }
         continue;
       }
       int settled = 0;
+      float v = INFINITY;
       if (lane == 0) {
         if (MODE == MODE_CD) {
           hitp[pose] = 0;
@@ -1067,12 +1074,20 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
           if (BATCH && anyp) settled = *reinterpret_cast<volatile uint8_t *>(&anyp[pose]);
         } else {
           distp[pose] = INFINITY;
+          if (BATCH && mindp) v = *reinterpret_cast<volatile float *>(&mindp[pose]);
         }
       }
       if (BATCH && MODE == MODE_CD && __shfl_sync(kFull, settled, 0)) continue;  // the set's answer is known
+      if (BATCH && MODE == MODE_PQ) {
+        best = __shfl_sync(kFull, v, 0);  // the set's best so far bounds this item too
+        if (best == 0.f) continue;
+      }
     } else if (MODE == MODE_PQ) {
       float v = 0.f;
-      if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
+      if (lane == 0) {
+        v = *reinterpret_cast<volatile float *>(&distp[pose]);
+        if (BATCH && mindp) v = fminf(v, *reinterpret_cast<volatile float *>(&mindp[pose]));
+      }
       best = __shfl_sync(kFull, v, 0);
       if (task_lb >= best) continue;  // a closer pair was found after this one was handed on
     } else if (early) {
@@ -1083,8 +1098,6 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       }
       if (__shfl_sync(kFull, h, 0)) continue;
     }
-    float published = best;
-
     int sp = 0, nleaf = 0;
     uint32_t nhits = 0;
     bool done = false;
@@ -1132,10 +1145,14 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
       } else {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dl = fminf(dl, __shfl_xor_sync(kFull, dl, o));
-        best = fminf(best, dl);
-        if (best < published) {
-          if (lane == 0) atomicMin(reinterpret_cast<unsigned int *>(&distp[pose]), __float_as_uint(best));
-          published = best;
+        // a distance this task found below every bound it knows is published at once (to the
+        // set's minimum too); the pose's output only ever receives distances of its own pairs
+        if (dl < best) {
+          best = dl;
+          if (lane == 0) {
+            atomicMin(reinterpret_cast<unsigned int *>(&distp[pose]), __float_as_uint(best));
+            if (BATCH && mindp) atomicMin(reinterpret_cast<unsigned int *>(&mindp[pose]), __float_as_uint(best));
+          }
         }
         if (best == 0.f) done = true;
       }
@@ -1343,7 +1360,10 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
         if (!stop && (expansions & (early ? 3 : 15)) == 0) {
           if (MODE == MODE_PQ) {
             float v = 0.f;
-            if (lane == 0) v = *reinterpret_cast<volatile float *>(&distp[pose]);
+            if (lane == 0) {
+              v = *reinterpret_cast<volatile float *>(&distp[pose]);
+              if (BATCH && mindp) v = fminf(v, *reinterpret_cast<volatile float *>(&mindp[pose]));
+            }
             best = fminf(best, __shfl_sync(kFull, v, 0));
           } else if (early) {
             int h = 0;
@@ -1398,8 +1418,6 @@ __global__ void __launch_bounds__(kThreads, CBVH_MIN_BLOCKS(MODE, BATCH)) traver
           if (BATCH && anyp) anyp[pose] = 1;
           if (p.counts) atomicAdd(&p.counts[pose], nhits);
         }
-      } else if (best < published) {
-        atomicMin(reinterpret_cast<unsigned int *>(&distp[pose]), __float_as_uint(best));
       }
     }
     __syncwarp();
@@ -2268,6 +2286,7 @@ struct cbvh_batch {
   std::vector<BatchItem> items;
   std::vector<unsigned long long> bases;
   std::vector<std::pair<uint8_t *, int64_t>> any_hit;  // distinct per-set flag arrays, cleared at launch
+  std::vector<std::pair<float *, int64_t>> min_dist;   // distinct per-set distance arrays, reset at launch
   std::vector<Group> groups;
   int64_t o_ctr = 0, o_items = 0, o_bases = 0, o_tasks0 = 0, o_tasks1 = 0, o_ready = 0, o_stacks = 0, total = 0;
   uint32_t task_cap = 0;
@@ -2291,10 +2310,13 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
     if (x.flags & ~CBVH_EARLY_EXIT) return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": unknown flags");
     if (x.any_hit && x.mode != 0)
       return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": any_hit is for collision queries");
-    for (int64_t k = 0; k < i && x.any_hit; ++k)
-      if (q[k].any_hit == x.any_hit && q[k].n != x.n)
+    if (x.min_dist && x.mode != 1)
+      return cbvh::fail(CBVH_ERR_ARG, "query " + std::to_string(i) + ": min_dist is for distance queries");
+    for (int64_t k = 0; k < i; ++k)
+      if ((x.any_hit && q[k].any_hit == x.any_hit && q[k].n != x.n) ||
+          (x.min_dist && q[k].min_dist == x.min_dist && q[k].n != x.n))
         return cbvh::fail(CBVH_ERR_ARG, "queries " + std::to_string(k) + " and " + std::to_string(i) +
-                                            " share any_hit but differ in pose count");
+                                            " share a set's array but differ in pose count");
   }
   auto b = new cbvh_batch();
   if (int rc = device_sms(&b->sms)) {
@@ -2329,6 +2351,7 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
         it.dist = x.dist;
         it.flags = x.mode == 0 ? (x.flags | CBVH_EARLY_EXIT) : 0;  // collision items return flags only
         it.any_hit = x.mode == 0 ? x.any_hit : nullptr;
+        it.min_dist = x.mode == 1 ? x.min_dist : nullptr;
         b->items.push_back(it);
         b->bases.push_back(acc);
         acc += (unsigned long long)x.n;
@@ -2360,14 +2383,22 @@ extern "C" int cbvh_batch_create(const cbvh_query_t *q, int64_t nq, cbvh_batch *
       it.hit = nullptr;  // set at upload: the group's intersection flags + item base
       it.flags = CBVH_EARLY_EXIT;
       it.any_hit = nullptr;
+      it.min_dist = nullptr;
       b->items.push_back(it);
     }
   }
   for (int64_t i = 0; i < nq; ++i) {
-    if (!q[i].any_hit || q[i].n == 0) continue;
+    if (q[i].n == 0) continue;
     bool seen = false;
-    for (const auto &a : b->any_hit) seen |= a.first == q[i].any_hit;
-    if (!seen) b->any_hit.emplace_back(q[i].any_hit, q[i].n);
+    if (q[i].any_hit) {
+      for (const auto &a : b->any_hit) seen |= a.first == q[i].any_hit;
+      if (!seen) b->any_hit.emplace_back(q[i].any_hit, q[i].n);
+    }
+    seen = false;
+    if (q[i].min_dist) {
+      for (const auto &a : b->min_dist) seen |= a.first == q[i].min_dist;
+      if (!seen) b->min_dist.emplace_back(q[i].min_dist, q[i].n);
+    }
   }
   // workspace plan
   int64_t o = kWsHeader;
@@ -2444,6 +2475,10 @@ extern "C" int cbvh_batch_launch(const cbvh_batch *b, void *workspace, int64_t w
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
   for (const auto &a : b->any_hit)
     if (e == cudaSuccess) e = cudaMemsetAsync(a.first, 0, (size_t)a.second, s);
+  // 0x7f7f7f7f = 3.4e38: larger than any distance, and below +inf under the unsigned
+  // ordering that atomicMin applies to non-negative floats
+  for (const auto &a : b->min_dist)
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.first, 0x7f, 4 * (size_t)a.second, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   const BatchItem *dev_items = reinterpret_cast<const BatchItem *>(ws + b->o_items);
   const unsigned long long *dev_bases = reinterpret_cast<const unsigned long long *>(ws + b->o_bases);

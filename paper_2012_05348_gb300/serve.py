@@ -13,7 +13,8 @@ A robot is either one hierarchy or a chain of links (``robots``: name -> link mo
 a request for a chain carries one pose per link and configuration, runs as one batch item
 per link, and resolves to "any link collides" or "smallest distance over the links".  The
 links of a collision request form one configuration set of the batch, so a configuration
-stops at its first colliding link.
+stops at its first colliding link; the links of a distance request share the
+configuration's best distance, with which each link's branch and bound prunes.
 
 A batch whose device status reports an error (for example a node-pair stack or a wait that
 ran out) does not fail its requests at once: each is retried once on the plain path, one
@@ -201,17 +202,17 @@ class Server:
             items, o = [], 0
             for r, name, P in parts:
                 n = len(P)
-                chain_cd = r.kind == "collide" and len(self.links(r.robot)) > 1
+                chain = len(self.links(r.robot)) > 1
                 items.append(dict(A=self.models[r.env], B=self.models[name], kind=r.kind,
-                                  poses=dev[o:o + n], early_exit=r.early_exit, set=id(r) if chain_cd else None))
+                                  poses=dev[o:o + n], early_exit=r.early_exit, set=id(r) if chain else None))
                 o += n
             batch = Batch(items, device=self.device)
             batch.launch(stream)
             outs, k = [], 0
             for r in reqs:
                 nl = len(self.links(r.robot))
-                if r.kind == "collide" and nl > 1:  # the configuration set's answer
-                    srcs = [batch.any_hit[id(r)]]
+                if nl > 1:  # the configuration set's answer
+                    srcs = [batch.any_hit[id(r)] if r.kind == "collide" else batch.min_dist[id(r)]]
                 else:
                     srcs = batch.outputs[k:k + nl]
                 k += nl

@@ -179,6 +179,36 @@ def test_arm_sweep_full_clutter_against_oracle(cb, m, tb):
         assert souts.sum() < outs.sum()  # configurations stopped at their first colliding link
 
 
+def test_distance_sets_against_oracle(cb, scene):
+    """The arm's clearance: distance items of the six links as one configuration set share
+    the configuration's best distance.  The set's minimum equals the smallest of the
+    oracle's per-link distances within 1e-5 D, and every item's own output is at least its
+    oracle distance (an upper bound, exact where it is the set's minimum); two launches in a
+    row give the same minima."""
+    import torch
+    c3 = scene["c3"]
+    n = 60
+    LP = [torch.as_tensor(np.ascontiguousarray(c3["link_poses"][:n, i]), device="cuda") for i in range(6)]
+    items = [dict(A=scene["clutter"], B=L, kind="distance", poses=P, set="arm") for L, P in zip(scene["links"], LP)]
+    batch = cb.Batch(items)
+    va = c3["A"][0]
+    A = oracle.BVH(*c3["A"], 24, 8, 8, 16384)
+    o_d = []
+    D = 0.0
+    for i, (v, t) in enumerate(c3["links"]):
+        B = oracle.BVH(v, t, 24, 8, 8, 16384)
+        o_d.append(oracle.distance(A, B, c3["link_poses"][:n, i])[0])
+        D = max(D, synth.scene_diameter(va, v))
+    o_d = np.stack(o_d)
+    for _ in range(2):
+        outs = np.stack([o.cpu().numpy() for o in batch.run()]).astype(np.float64)
+        mind = batch.min_dist["arm"].cpu().numpy().astype(np.float64)
+        assert np.abs(mind - o_d.min(0)).max() <= 1e-5 * D
+        assert (outs >= o_d - 1e-5 * D).all()
+        assert np.allclose(outs.min(0), mind, rtol=0, atol=1e-5 * D)
+    assert (o_d.min(0) > 0).sum() >= 5
+
+
 def test_arm_self_collision_against_oracle(cb, scene):
     """Self-collision of the arm: every non-adjacent link pair, link j posed in link i's
     frame, all in one batch; flags match the oracle on configurations away from contact."""
