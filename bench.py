@@ -297,12 +297,12 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
         # self-collision: every non-adjacent link pair, link j posed in link i's frame
         sp = synth.self_pairs(6)
         rel = [torch.as_tensor(synth.relative_poses(c["link_poses"], i, j), device=dev) for i, j in sp]
-        self_items = [dict(A=links[i], B=links[j], kind="collide", poses=R, early_exit=True)
+        self_items = [dict(A=links[i], B=links[j], kind="collide", poses=R, early_exit=True, set="self")
                       for (i, j), R in zip(sp, rel)]
         self_batch = cb.Batch(self_items, device=dev)
-        self_outs = self_batch.run()
+        self_batch.run()
         ms_self = _events_ms(self_batch.run, torch)
-        self_cfg = np.stack([o.cpu().numpy() for o in self_outs]).any(0)
+        self_cfg = self_batch.any_hit["self"].cpu().numpy().astype(bool)
 
         # clearance: the smallest distance over the six links of each configuration, as one
         # distance set (each link prunes with the configuration's best so far), against the

@@ -234,6 +234,11 @@ def test_arm_self_collision_against_oracle(cb, scene):
     assert checked > 600
     hits = np.stack(outs).any(0)
     assert 0 < hits.sum() < n  # some configurations fold onto themselves, some do not
+    # the ten link pairs as one configuration set: the set's flag is the configuration's
+    # answer (some pair of links intersects), equal to the pairs' flags taken one by one
+    sb = cb.Batch([dict(it, set="self") for it in items])
+    sb.run()
+    assert (sb.any_hit["self"].cpu().numpy().astype(bool) == hits).all()
 
 
 def test_batch_refuses_stream_vbyte_hierarchies(cb, scene):
