@@ -303,6 +303,14 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
         self_batch.run()
         ms_self = _events_ms(self_batch.run, torch)
         self_cfg = self_batch.any_hit["self"].cpu().numpy().astype(bool)
+        # validity in one launch: the six links against the scene and the ten link pairs
+        # against each other as one configuration set (a configuration is invalid once any
+        # of the sixteen items intersects)
+        valid_batch = cb.Batch([dict(it, set="valid") for it in items] +
+                               [dict(it, set="valid") for it in self_items], device=dev)
+        valid_batch.run()
+        ms_valid = _events_ms(valid_batch.run, torch)
+        invalid_cfg = valid_batch.any_hit["valid"].cpu().numpy().astype(bool)
 
         # clearance: the smallest distance over the six links of each configuration, as one
         # distance set (each link prunes with the configuration's best so far), against the
@@ -349,6 +357,12 @@ def arm_sweep(cb, torch, dev, n_configs, tune_configs=20000):
                                "configs_self_colliding": int(self_cfg.sum()), "ms": ms_self,
                                "pair_queries_per_s": len(sp) * n_configs / (ms_self / 1e3)},
             "configs_free": int((~collide_cfg & ~self_cfg).sum()),
+            "validity": {"items": len(items) + len(self_items), "ms": ms_valid,
+                         "configurations_per_s": n_configs / (ms_valid / 1e3),
+                         "configs_valid": int((~invalid_cfg).sum()),
+                         "equals_separate_sets": bool((invalid_cfg == (collide_cfg | self_cfg)).all()),
+                         "what": "links against the scene and link pairs against each other, one set per "
+                                 "configuration, one launch"},
             "batched_link_queries_per_s": q / (ms_batched / 1e3), "batched_ms": ms_batched,
             "batched_latency_ms": dict(lat_batched, per="graph replay of the whole sweep"),
             "plain_link_queries_per_s": q / (ms_plain / 1e3), "plain_ms": ms_plain,

@@ -239,6 +239,14 @@ def test_arm_self_collision_against_oracle(cb, scene):
     sb = cb.Batch([dict(it, set="self") for it in items])
     sb.run()
     assert (sb.any_hit["self"].cpu().numpy().astype(bool) == hits).all()
+    # validity: the links against the clutter and the link pairs against each other in one
+    # set; the answer is the OR of both, each computed on its own
+    env = [dict(A=scene["clutter"], B=scene["links"][i], kind="collide", early_exit=True,
+                poses=torch.as_tensor(np.ascontiguousarray(c3["link_poses"][:n, i]), device="cuda")) for i in range(6)]
+    env_hits = np.stack([o.cpu().numpy() for o in cb.Batch(env).run()]).any(0)
+    vb = cb.Batch([dict(it, set="valid") for it in env + items])
+    vb.run()
+    assert (vb.any_hit["valid"].cpu().numpy().astype(bool) == (env_hits | hits)).all()
 
 
 def test_batch_refuses_stream_vbyte_hierarchies(cb, scene):
